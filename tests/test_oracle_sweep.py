@@ -1,0 +1,111 @@
+"""Pins of the parallel swap optimiser (Sec. 3.4) as run by the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import FLAG_COMMITTED, FLAG_IMPROVING, FLAG_TIE, FLAG_VALID
+from tests._independent import half_plane_area, torus_d2_bruteforce, torus_gaussian_blur
+
+
+def _run(tile, n):
+    logs, energies = [], [tile.energy()]
+    for _ in range(n):
+        logs.append(tile.sweep())
+        energies.append(tile.energy())
+    return logs, energies
+
+
+@pytest.mark.parametrize("objective", [oracle.OBJECTIVE_BLUE, oracle.OBJECTIVE_LITERAL])
+def test_objective_monotone_and_changes_add_up(objective):
+    """Kept couples never interact, so the change of Eq. 1 over a pass is exactly the sum of the
+    kept couples' changes, and every kept change improves the objective."""
+    t = oracle.OracleTile(32, 32, 16, 64, seed=1, objective=objective)
+    logs, E = _run(t, 60)
+    for s, lg in enumerate(logs):
+        kept = (lg.flags & FLAG_COMMITTED) != 0
+        assert np.all(objective * lg.dE[kept] < 0)
+        assert abs((E[s + 1] - E[s]) - lg.dE[kept].sum()) <= 1e-9 * E[s]
+        assert objective * (E[s + 1] - E[s]) <= 1e-9 * E[s]
+    assert objective * (E[-1] - E[0]) < 0
+
+
+def test_resolve_rule_against_bruteforce():
+    W = H = 24
+    t = oracle.OracleTile(W, H, 16, 32, seed=4)
+    r2 = t.r * t.r
+    for s in range(8):
+        lg = t.sweep()
+        imp = np.nonzero(lg.flags & FLAG_IMPROVING)[0]
+        key = {int(j): oracle.priority_key(t.seed, t.pair, s, int(j)) for j in imp}
+
+        def interact(i, j):
+            return any(torus_d2_bruteforce(W, H, int(p), int(q)) <= r2
+                       for p in lg.couples[i] for q in lg.couples[j])
+
+        for j in imp:
+            beaten = any(i != j and interact(i, j) and key[int(i)] > key[int(j)] for i in imp)
+            assert bool(lg.flags[j] & FLAG_COMMITTED) == (not beaten)
+        # kept couples are pairwise further apart than r
+        kept = np.nonzero(lg.flags & FLAG_COMMITTED)[0]
+        for x in range(len(kept)):
+            for y in range(x + 1, len(kept)):
+                assert not interact(kept[x], kept[y])
+        # nothing non-improving is kept
+        assert not np.any(((lg.flags & FLAG_COMMITTED) != 0) & ((lg.flags & FLAG_IMPROVING) == 0))
+
+
+def test_swaps_move_counts_with_their_shifts():
+    t = oracle.OracleTile(20, 20, 16, 24, seed=2)
+    _run(t, 30)
+    assert sorted(t.sidx.tolist()) == list(range(t.P))
+    recount = oracle.counts(t.N, t.g, t.U[t.sidx], t.a, t.b, t.C)
+    assert np.array_equal(recount, t.k)
+    u = t.shifts_float().reshape(-1, 2).astype(np.float64)
+    assert np.array_equal(u * 2**32, t.U[t.sidx].astype(np.float64))
+
+
+def test_padded_tile_drops_out_of_range_couples():
+    t = oracle.OracleTile(12, 10, 16, 8, seed=3)     # P = 120, padded to 128
+    assert t.L == 7 and t.M == 16
+    for _ in range(10):
+        lg = t.sweep()
+        out = (lg.couples >= t.P).any(axis=1)
+        assert np.array_equal((lg.flags & FLAG_VALID) == 0, out)
+        assert np.all(lg.flags[out] == 0)
+
+
+def test_lockstep_override_only_on_ties():
+    t1 = oracle.OracleTile(16, 16, 16, 16, seed=5)
+    t2 = oracle.OracleTile(16, 16, 16, 16, seed=5)
+    everything = np.ones(t1.M, np.uint8)
+    a = t1.sweep(gpu_improving=everything)                # margin 1e-6: (almost) no ties
+    b = t2.sweep(gpu_improving=everything, tie_rel=10.0)  # every valid couple with S>0 ties
+    ties_a = (a.flags & FLAG_TIE) != 0
+    assert np.all(np.abs(a.dE[ties_a]) < 1e-6 * a.S[ties_a])
+    tied = (b.flags & FLAG_TIE) != 0
+    assert np.all((b.flags[tied] & FLAG_IMPROVING) != 0)
+    untied_valid = ((b.flags & FLAG_VALID) != 0) & ~tied
+    assert np.all(b.S[untied_valid] == 0)
+
+
+def _blurred_rmse(t, sigma_b):
+    ref = np.array([half_plane_area(float(a), float(b), float(c) / 2**24)
+                    for a, b, c in zip(t.a, t.b, t.C)])
+    err = (t.k / t.N - ref).reshape(t.H, t.W, t.T)
+    return float(np.sqrt((torus_gaussian_blur(err, sigma_b) ** 2).mean()))
+
+
+def test_blue_objective_improves_blurred_error_and_literal_worsens_it():
+    """Sec. 3.3 criterion: RMSE of the Gaussian-blurred estimate tile.  Raising Eq. 1 spreads
+    the error as blue noise and lowers it; reducing Eq. 1 as printed raises it."""
+    res = {}
+    for objective in (oracle.OBJECTIVE_BLUE, oracle.OBJECTIVE_LITERAL):
+        t = oracle.OracleTile(32, 32, 16, 64, seed=0, objective=objective)
+        before = _blurred_rmse(t, 2.0)
+        for _ in range(400):
+            t.sweep()
+        res[objective] = (before, _blurred_rmse(t, 2.0))
+    b0, b1 = res[oracle.OBJECTIVE_BLUE]
+    l0, l1 = res[oracle.OBJECTIVE_LITERAL]
+    assert b1 < 0.8 * b0
+    assert l1 > 1.2 * l0
