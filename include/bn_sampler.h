@@ -1,0 +1,195 @@
+/*
+ * bn_sampler.h — C ABI of the GB300 (sm_103a) screen-space blue-noise sampler optimizer.
+ *
+ * Method: Belcour & Heitz, "Lessons Learned and Improvements when Building Screen-Space
+ * Samplers with Blue-Noise Error Distribution" (SIGGRAPH '21 Talks).
+ *   - Sec. 2:   a screen-space sampler is a main sequence s^k scrambled per pixel by u_p; the
+ *               tile U = {u_p} is optimised against the Eq. 1 loss over the map of test-
+ *               integrand estimates I_p (random Heavisides, Fig. 1b).
+ *   - Sec. 3.2: main sequence = rank-1 lattice s^k = mod(Phi(k) d, 1), scrambling =
+ *               toroidal (Cranley-Patterson) shift mod(s^k + u_p, 1).
+ *   - Sec. 3.4: parallel optimisation: many disjoint couples of pixels are tested for a swap
+ *               in each pass; candidates come from a precomputed permutation of pixel indices
+ *               XOR-scrambled with a per-pass value.
+ *
+ * Conventions
+ *   - Every call returns BN_OK (0) or a negative BN_ERR_* code; bn_last_error() then returns a
+ *     thread-local message.  No C++ exception crosses this boundary.
+ *   - All device work of a sampler is enqueued on the CUDA stream given to bn_sampler_init
+ *     (NULL = the legacy default stream).  Calls that return data to the host synchronise that
+ *     stream; the others only enqueue.
+ *   - The library owns all device state it allocates (cudaMalloc at init, cudaFree at destroy).
+ *     Host output buffers are owned by the caller and must hold the stated number of elements.
+ *   - Pixel p = y * width + x.  Per-pixel arrays are row-major [height][width].
+ *   - One sampler holds n_pairs independent 2-D problems ("pairs of dimensions", Sec. 3.1):
+ *     each pair has its own shifts, integrands, estimates and optimisation state; pair i uses
+ *     Philox streams with pair index i.
+ */
+#ifndef BN_SAMPLER_H
+#define BN_SAMPLER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------------------ */
+#define BN_OK 0
+#define BN_ERR_INVALID_ARG (-1) /* a parameter is out of range or a pointer is NULL        */
+#define BN_ERR_OOM (-2)         /* a device allocation failed                              */
+#define BN_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed             */
+#define BN_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out (grid barrier)       */
+#define BN_ERR_BUSY (-5)        /* the server refused a request (memory budget / slots)    */
+#define BN_ERR_BAD_STATE (-6)   /* the object is not in a state that allows this call      */
+
+/* ---- optimisation options ----------------------------------------------------------------- */
+/* Commit rule of one pass (Sec. 3.4).  NONINTERACTING keeps, among improving couples whose
+ * pixels lie within the weight radius of each other, only the couple of highest priority, so
+ * the kept changes add up exactly and the objective never gets worse.  CONCURRENT keeps every
+ * improving couple, as the paper describes its GPU optimiser (the loss may then move the wrong
+ * way early on, as the paper notes). */
+#define BN_MODE_NONINTERACTING 0
+#define BN_MODE_CONCURRENT 1
+
+/* Direction of the optimisation of Eq. 1.  A swap keeps sum_p |I_p|^2 fixed, so raising Eq. 1
+ * lowers the Gaussian-weighted correlation of neighbouring estimates: the error becomes blue
+ * noise (BLUE, the default).  LITERAL reduces Eq. 1 as printed. */
+#define BN_OBJECTIVE_BLUE (-1)
+#define BN_OBJECTIVE_LITERAL 1
+
+/* How sweeps are executed (results are identical; only speed differs). */
+#define BN_SCHEDULE_AUTO 0       /* persistent when the tile allows it, else plain          */
+#define BN_SCHEDULE_PLAIN 1      /* three launches per sweep, one warp per couple           */
+#define BN_SCHEDULE_PERSISTENT 2 /* one cooperative launch for many sweeps, SMEM-blocked    */
+
+typedef struct bn_config {
+    int32_t width, height;     /* toroidal tile, 2..4096 each, width*height <= 2^22          */
+    int32_t n_points;          /* N = 2^m lattice points per pixel, 2..1024                  */
+    int32_t generator_g;       /* Korobov generator, odd, < N; 0 = max-min-distance choice   */
+    int32_t n_pairs;           /* 1 (2-D) or 2 (4-D as two independent pairs, Sec. 3.1)      */
+    int32_t n_integrands;      /* T Heavisides per pair, 1..4096                             */
+    float sigma;               /* Eq. 1 weight exp(-d^2 / sigma^2); the paper uses 2.1       */
+    int32_t radius;            /* weight cut-off: pairs with d^2 <= radius^2, 1..8           */
+    int32_t couples_per_sweep; /* couples tested per pass; 0 = 2^ceil(log2 P) / 8 (N/4 px)   */
+    int32_t mode;              /* BN_MODE_*                                                  */
+    int32_t objective;         /* BN_OBJECTIVE_*; 0 = BN_OBJECTIVE_BLUE                      */
+    int32_t schedule;          /* BN_SCHEDULE_*                                              */
+    uint64_t seed;             /* key of every Philox stream of this sampler                 */
+} bn_config;
+/* Further limit: 24 * T * N^2 < 2^31 (exact int32 accumulation of the swap energy terms). */
+
+typedef struct bn_sweep_stats {
+    int64_t sweeps;     /* passes run by the call (per pair)                                  */
+    int64_t proposals;  /* valid couples evaluated, all pairs                                 */
+    int64_t improving;  /* couples whose swap improves the objective                          */
+    int64_t committed;  /* swaps applied                                                       */
+    int64_t ties;       /* couples with |dL| < 1e-6 * sum of |per-distance terms| (fp32 view) */
+} bn_sweep_stats;
+
+typedef struct bn_info {
+    int32_t generator_g;     /* g actually used                                              */
+    int32_t log2_padded;     /* L: candidate indices live in [0, 2^L), 2^L >= P              */
+    int32_t couples;         /* couples per pass (M)                                         */
+    int32_t count_bytes;     /* 1 (N <= 64) or 2 bytes per stored count                      */
+    int32_t row_bytes;       /* bytes of one pixel's count vector (T padded to 128 B)        */
+    int32_t n_offsets;       /* distinct neighbours within the radius                        */
+    int32_t n_classes;       /* distinct squared distances among them                        */
+    int32_t schedule;        /* schedule that optimize_sweeps will use                       */
+    int64_t sweep;           /* passes done so far (per pair)                                */
+    int64_t device_bytes;    /* device memory held by the sampler                            */
+} bn_info;
+
+typedef struct bn_sampler bn_sampler;
+
+/* Create a sampler and run its initialisation on the stream (Sec. 2, Sec. 3.2): pick g, draw
+ * the shifts u_p, the Heaviside bank and the candidate permutation, and count, for every pixel
+ * and integrand, the lattice points under the Heaviside (k_p[t], estimate k/N).
+ * cfg: read only, copied.  cuda_stream: a cudaStream_t or NULL.  out: receives the handle. */
+int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out);
+
+/* Eq. 1 for every pair: L = sum_p sum_{q != p, d(p,q) <= r} exp(-d^2/sigma^2) |I_p - I_q|^2
+ * over ordered pairs, distances on the torus.  Exact integer sums per squared distance, then
+ * an fp32 compensated weighted sum.  energy_per_pair: host, n_pairs doubles.  Synchronises. */
+int bn_evaluate_energy(bn_sampler *s, double *energy_per_pair);
+
+/* Run n_sweeps passes of the parallel swap optimiser (Sec. 3.4) on every pair; the pass
+ * counter persists, so two calls of a and b passes equal one call of a + b.  stats: host,
+ * nullable; when given the call synchronises and fills it. */
+int bn_optimize_sweeps(bn_sampler *s, int32_t n_sweeps, bn_sweep_stats *stats);
+
+/* The optimised tile u_p as float [n_pairs][height][width][2] (exact: 24-bit fixed point).
+ * out: host (out_is_device = 0, synchronises) or device (1, enqueued) buffer of n_floats >=
+ * n_pairs * width * height * 2 floats. */
+int bn_fetch_shifts(bn_sampler *s, float *out, size_t n_floats, int out_is_device);
+
+/* Re-run the initialisation with a new seed (same geometry), without allocating: the problem
+ * descriptors are copied from pinned host memory, then shifts, integrands, permutation and
+ * counts are rebuilt and the pass counter returns to 0.  Enqueued only. */
+int bn_sampler_reset(bn_sampler *s, uint64_t seed);
+
+/* Free all device state.  Synchronises the sampler's stream first.  NULL is allowed. */
+void bn_sampler_destroy(bn_sampler *s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bn_last_error(void);
+
+/* ---- inspection, parity and checkpoint -------------------------------------------------- */
+int bn_get_info(bn_sampler *s, bn_info *info);
+
+/* The shifted lattice s^k_p of one pixel (Sec. 3.2, Fig. 1a) as float [N][2] in [0, 1).
+ * Computed on the device from the same fixed-point values the counting kernel uses.  Host
+ * buffer of n_floats >= 2 N.  Synchronises. */
+int bn_fetch_points(bn_sampler *s, int32_t pair, int32_t pixel, float *out, size_t n_floats);
+
+/* Counts k_p[t] of one pair as int32 [P][T] (host, n >= P*T).  Synchronises. */
+int bn_fetch_counts(bn_sampler *s, int32_t pair, int32_t *out, size_t n);
+
+/* The Heaviside bank of one pair: a[T], b[T] (int32) and C[T] (int64, c * 2^24); the
+ * integrand is [a x + b y < c].  Host buffers of T elements.  Synchronises. */
+int bn_fetch_integrands(bn_sampler *s, int32_t pair, int32_t *a, int32_t *b, int64_t *C,
+                        size_t T);
+
+/* Candidate permutation of one pair: int32 [2^L] (host).  Synchronises. */
+int bn_fetch_permutation(bn_sampler *s, int32_t pair, int32_t *out, size_t n);
+
+/* Log of the last pass of one pair: per couple j < M the change dL_j of Eq. 1 (float; 0 for
+ * dropped couples), flags (1 valid, 2 improving, 4 committed, 8 tie in fp32) and the couple's
+ * pixels (int32 [M][2]).  Any pointer may be NULL.  cap >= M.  Synchronises. */
+int bn_fetch_sweep_log(bn_sampler *s, int32_t pair, float *dE, uint8_t *flags,
+                       int32_t *couples, size_t cap);
+
+/* Checkpoint: the pass counter and, per pair, the index of the initial shift now at each
+ * pixel (int32 [n_pairs][P]).  get synchronises; set re-derives the counts from the shifts
+ * and enqueues. */
+int bn_get_state(bn_sampler *s, int64_t *sweep, int32_t *shift_index, size_t n);
+int bn_set_state(bn_sampler *s, int64_t sweep, const int32_t *shift_index, size_t n);
+
+/* ---- kernel timing ------------------------------------------------------------------------ */
+/* When enabled, every sweep kernel launched for this sampler (or a batch containing it) is
+ * bracketed by CUDA events on its stream; bn_kernel_times then returns, per kernel name, the
+ * number of launches and their summed device time since the last read (and resets them).
+ * Synchronises. */
+typedef struct bn_kernel_time {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} bn_kernel_time;
+int bn_set_kernel_timing(bn_sampler *s, int enable);
+int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_out);
+
+/* ---- batches: many samplers swept together in one launch sequence ------------------------- */
+typedef struct bn_batch bn_batch;
+
+/* Group samplers (all created on the same device) so that their sweeps run fused: every pair
+ * of every sampler becomes one problem of a single launch.  The batch uses its own stream
+ * (cuda_stream) and records events to order itself after each member's stream. */
+int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out);
+int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats);
+void bn_batch_destroy(bn_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BN_SAMPLER_H */

@@ -1,0 +1,10 @@
+"""GB300-native optimiser of screen-space blue-noise samplers built from a rank-1 lattice with
+per-pixel toroidal shifts (Belcour & Heitz, SIGGRAPH '21 Talks).
+
+The computation lives in ``libbnsampler.so`` (CUDA, sm_103a), reached through the C ABI of
+``include/bn_sampler.h``; this package only marshals arguments.
+"""
+from ._lib import (BN_MODE_CONCURRENT, BN_MODE_NONINTERACTING, BN_OBJECTIVE_BLUE,  # noqa: F401
+                   BN_OBJECTIVE_LITERAL, BN_SCHEDULE_AUTO, BN_SCHEDULE_PERSISTENT,
+                   BN_SCHEDULE_PLAIN, BnError, load)
+from .sampler import Batch, Sampler, SweepStats  # noqa: F401

@@ -1,0 +1,674 @@
+// bn_api.cu — host runtime behind the C ABI declared in include/bn_sampler.h: validation,
+// device memory, problem descriptors, and the call sequences of init / sweeps / fetches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bn_launch.h"
+#include "bn_sampler.h"
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+#define BN_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? BN_ERR_OOM : BN_ERR_CUDA,          \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,    \
+                        __LINE__);                                                           \
+    } while (0)
+
+int log2_ceil(long long n)
+{
+    int L = 0;
+    while ((1ll << L) < n) ++L;
+    return L;
+}
+
+int64_t gcd64(int64_t a, int64_t b)
+{
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Korobov generator with the largest toroidal minimum distance (ties: smallest g), Sec. 3.2
+int korobov_g(int N)
+{
+    int best_g = 1;
+    long long best = -1;
+    for (int g = 1; g < N; ++g) {
+        if (gcd64(g, N) != 1) continue;
+        long long d = -1;
+        for (long long k = 1; k < N; ++k) {
+            long long x = k, y = (k * g) % N;
+            long long dx = x < N - x ? x : N - x, dy = y < N - y ? y : N - y;
+            long long d2 = dx * dx + dy * dy;
+            if (d < 0 || d2 < d) d = d2;
+        }
+        if (d > best) {
+            best = d;
+            best_g = g;
+        }
+    }
+    return best_g;
+}
+
+struct Slab {
+    char *base = nullptr;
+    size_t used = 0, cap = 0;
+    template <typename T>
+    T *take(size_t n)
+    {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + n * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + off) : nullptr;
+    }
+};
+
+}  // namespace
+
+struct bn_sampler {
+    bn_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_prob = 0;
+    std::vector<bn::Problem> hprob;
+    bn::Problem *dprob = nullptr;
+    char *slab = nullptr;
+    size_t slab_bytes = 0;
+    double *h_energy = nullptr;  // pinned, [n_prob]
+    int64_t sweep = 0;           // host mirror of the pass counter
+    int schedule = BN_SCHEDULE_PLAIN;
+    bn::Problem *h_pinned = nullptr;  // pinned staging of the descriptors (reset)
+    bn::KernelTimer timer;
+};
+
+struct bn_batch {
+    std::vector<bn_sampler *> members;
+    cudaStream_t stream = nullptr;
+    bn::Problem *dprob = nullptr;
+    int n_prob = 0;
+    int max_M = 0;
+    int count_bytes = 1;
+    bn::KernelTimer *timer = nullptr;  // the first member's timer
+};
+
+namespace {
+
+int validate(const bn_config &c)
+{
+    if (c.width < 2 || c.height < 2 || c.width > 4096 || c.height > 4096)
+        return fail(BN_ERR_INVALID_ARG, "width/height must be in [2, 4096] (got %d x %d)",
+                    c.width, c.height);
+    if ((long long)c.width * c.height > (1ll << 22))
+        return fail(BN_ERR_INVALID_ARG, "width*height must be <= 2^22");
+    if (c.n_points < 2 || c.n_points > 1024 || (c.n_points & (c.n_points - 1)))
+        return fail(BN_ERR_INVALID_ARG, "n_points must be a power of two in [2, 1024] (got %d)",
+                    c.n_points);
+    if (c.generator_g != 0 &&
+        (c.generator_g < 1 || c.generator_g >= c.n_points || gcd64(c.generator_g, c.n_points) != 1))
+        return fail(BN_ERR_INVALID_ARG, "generator_g must be 0 or coprime to N in [1, N)");
+    if (c.n_pairs != 1 && c.n_pairs != 2)
+        return fail(BN_ERR_INVALID_ARG, "n_pairs must be 1 or 2");
+    const int cb = c.n_points <= 64 ? 1 : 2;
+    if (c.n_integrands < 1 || (long long)c.n_integrands * cb > bn::kMaxRowBytes)
+        return fail(BN_ERR_INVALID_ARG, "n_integrands must be in [1, %d] for N = %d",
+                    bn::kMaxRowBytes / cb, c.n_points);
+    if (24.0 * c.n_integrands * (double)c.n_points * c.n_points >= 2147483648.0)
+        return fail(BN_ERR_INVALID_ARG, "24 * T * N^2 must be < 2^31 (exact int32 sums)");
+    if (!(c.sigma > 0.f) || !std::isfinite(c.sigma))
+        return fail(BN_ERR_INVALID_ARG, "sigma must be positive");
+    if (c.radius < 1 || c.radius > 8) return fail(BN_ERR_INVALID_ARG, "radius must be in [1, 8]");
+    const int L = log2_ceil((long long)c.width * c.height);
+    if (c.couples_per_sweep < 0 || c.couples_per_sweep > (1 << L) / 2)
+        return fail(BN_ERR_INVALID_ARG, "couples_per_sweep must be in [0, 2^L / 2]");
+    if (c.mode != BN_MODE_NONINTERACTING && c.mode != BN_MODE_CONCURRENT)
+        return fail(BN_ERR_INVALID_ARG, "unknown mode %d", c.mode);
+    if (c.objective != 0 && c.objective != BN_OBJECTIVE_BLUE && c.objective != BN_OBJECTIVE_LITERAL)
+        return fail(BN_ERR_INVALID_ARG, "unknown objective %d", c.objective);
+    if (c.schedule < BN_SCHEDULE_AUTO || c.schedule > BN_SCHEDULE_PERSISTENT)
+        return fail(BN_ERR_INVALID_ARG, "unknown schedule %d", c.schedule);
+    return BN_OK;
+}
+
+// Fill the geometry / stencil part of a problem descriptor.  The neighbourhood is every
+// distinct pixel q != p of the torus within min-image distance r; offsets are the min-image
+// representatives, sorted by squared distance (one class per distinct d^2).
+void describe(const bn_config &c, int pair, bn::Problem &h)
+{
+    memset(&h, 0, sizeof h);
+    h.W = c.width;
+    h.H = c.height;
+    h.P = c.width * c.height;
+    h.L = log2_ceil(h.P);
+    h.M = c.couples_per_sweep ? c.couples_per_sweep : ((1 << h.L) / 8 > 0 ? (1 << h.L) / 8 : 1);
+    h.N = c.n_points;
+    h.m = log2_ceil(c.n_points);
+    h.g = c.generator_g ? c.generator_g : korobov_g(c.n_points);
+    h.T = c.n_integrands;
+    h.count_bytes = c.n_points <= 64 ? 1 : 2;
+    h.row_bytes = (c.n_integrands * h.count_bytes + bn::kRowAlign - 1) / bn::kRowAlign *
+                  bn::kRowAlign;
+    h.radius = c.radius;
+    h.mode = c.mode;
+    h.objective = c.objective ? c.objective : BN_OBJECTIVE_BLUE;
+    h.pair = (uint32_t)pair;
+    h.seed_lo = (uint32_t)c.seed;
+    h.seed_hi = (uint32_t)(c.seed >> 32);
+    h.scale = 4.0f / ((float)c.n_points * (float)c.n_points);
+
+    auto canonical = [](int d, int n) {
+        int o = ((d % n) + n) % n;
+        int rep = (2 * o <= n) ? o : o - n;
+        return rep == d;
+    };
+    struct Off { int d2, dy, dx; };
+    std::vector<Off> offs;
+    const int r = c.radius;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+            if ((dx == 0 && dy == 0) || dx * dx + dy * dy > r * r) continue;
+            if (!canonical(dx, c.width) || !canonical(dy, c.height)) continue;
+            offs.push_back({dx * dx + dy * dy, dy, dx});
+        }
+    std::sort(offs.begin(), offs.end(), [](const Off &x, const Off &y) {
+        if (x.d2 != y.d2) return x.d2 < y.d2;
+        if (x.dy != y.dy) return x.dy < y.dy;
+        return x.dx < y.dx;
+    });
+    h.n_off = (int)offs.size();
+    int ncls = 0;
+    for (int i = 0; i < h.n_off; ++i) {
+        if (i == 0 || offs[i].d2 != offs[i - 1].d2) {
+            h.d2[ncls] = offs[i].d2;
+            h.w[ncls] = (float)std::exp(-(double)offs[i].d2 / ((double)c.sigma * c.sigma));
+            h.cls_start[ncls] = i;
+            ++ncls;
+        }
+        h.off[i] = (offs[i].dx & 0xFFFF) | (offs[i].dy << 16);
+    }
+    h.n_cls = ncls;
+    h.cls_start[ncls] = h.n_off;
+}
+
+// carve the device arrays of one problem out of a slab (sizes only when base is null)
+void carve(Slab &s, bn::Problem &h)
+{
+    h.counts = s.take<uint8_t>((size_t)h.P * h.row_bytes);
+    h.U = s.take<uint32_t>((size_t)h.P * 2);
+    h.sidx = s.take<int32_t>(h.P);
+    h.perm = s.take<int32_t>((size_t)1 << h.L);
+    h.perm_inv = s.take<int32_t>((size_t)1 << h.L);
+    h.ha = s.take<int32_t>(h.T);
+    h.hb = s.take<int32_t>(h.T);
+    h.hC = s.take<int64_t>(h.T);
+    h.owner = s.take<unsigned long long>((size_t)h.P * 2);
+    h.log_dE = s.take<float>(h.M);
+    h.log_flags = s.take<uint8_t>(h.M);
+    h.log_couples = s.take<int32_t>((size_t)h.M * 2);
+    h.side_cls = s.take<int32_t>((size_t)h.M * 2 * bn::kMaxClasses);
+    h.arrivals = s.take<int32_t>(h.M);
+    h.ctr = s.take<long long>(4);
+    h.stats = s.take<unsigned long long>(bn::kStatCount);
+    h.esum = s.take<unsigned long long>(bn::kMaxClasses);
+    h.energy_out = s.take<double>(1);
+}
+
+int check_pair(bn_sampler *s, int32_t pair)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    if (pair < 0 || pair >= s->n_prob) return fail(BN_ERR_INVALID_ARG, "pair out of range");
+    return BN_OK;
+}
+
+int set_device(const bn_sampler *s)
+{
+    int cur = -1;
+    BN_CUDA(cudaGetDevice(&cur));
+    if (cur != s->device) BN_CUDA(cudaSetDevice(s->device));
+    return BN_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *bn_last_error(void) { return g_error.c_str(); }
+
+int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
+{
+    if (!cfg || !out) return fail(BN_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    int rc = validate(*cfg);
+    if (rc) return rc;
+    auto *s = new bn_sampler();
+    s->cfg = *cfg;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->n_prob = cfg->n_pairs;
+    s->schedule = cfg->schedule == BN_SCHEDULE_PERSISTENT ? BN_SCHEDULE_PERSISTENT
+                                                          : BN_SCHEDULE_PLAIN;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return fail(BN_ERR_CUDA, "no CUDA device");
+    }
+    s->hprob.resize(s->n_prob);
+    Slab sizing;
+    for (int i = 0; i < s->n_prob; ++i) {
+        describe(*cfg, i, s->hprob[i]);
+        carve(sizing, s->hprob[i]);
+    }
+    s->slab_bytes = sizing.used + 256;
+    cudaError_t e = cudaMalloc(&s->slab, s->slab_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dprob, sizeof(bn::Problem) * s->n_prob);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_energy, sizeof(double) * s->n_prob);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_pinned, sizeof(bn::Problem) * s->n_prob);
+    if (e != cudaSuccess) {
+        bn_sampler_destroy(s);
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? BN_ERR_OOM : BN_ERR_CUDA,
+                    "device allocation of %zu bytes failed: %s", s->slab_bytes,
+                    cudaGetErrorString(e));
+    }
+    Slab real;
+    real.base = s->slab;
+    real.cap = s->slab_bytes;
+    for (int i = 0; i < s->n_prob; ++i) carve(real, s->hprob[i]);
+    e = cudaMemcpyAsync(s->dprob, s->hprob.data(), sizeof(bn::Problem) * s->n_prob,
+                        cudaMemcpyHostToDevice, s->stream);
+    for (int i = 0; i < s->n_prob && e == cudaSuccess; ++i) {
+        e = bn::launch_init_tables(s->dprob + i, s->hprob[i], s->stream);
+        if (e == cudaSuccess) e = bn::launch_counts(s->dprob + i, s->hprob[i], s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        bn_sampler_destroy(s);
+        return fail(BN_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return BN_OK;
+}
+
+void bn_sampler_destroy(bn_sampler *s)
+{
+    if (!s) return;
+    if (s->stream || s->slab) cudaStreamSynchronize(s->stream);
+    if (s->slab) cudaFree(s->slab);
+    if (s->dprob) cudaFree(s->dprob);
+    if (s->h_energy) cudaFreeHost(s->h_energy);
+    if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    delete s;
+}
+
+int bn_get_info(bn_sampler *s, bn_info *info)
+{
+    if (!s || !info) return fail(BN_ERR_INVALID_ARG, "null argument");
+    const bn::Problem &h = s->hprob[0];
+    info->generator_g = h.g;
+    info->log2_padded = h.L;
+    info->couples = h.M;
+    info->count_bytes = h.count_bytes;
+    info->row_bytes = h.row_bytes;
+    info->n_offsets = h.n_off;
+    info->n_classes = h.n_cls;
+    info->schedule = s->schedule;
+    info->sweep = s->sweep;
+    info->device_bytes = (int64_t)s->slab_bytes;
+    return BN_OK;
+}
+
+int bn_evaluate_energy(bn_sampler *s, double *energy_per_pair)
+{
+    if (!s || !energy_per_pair) return fail(BN_ERR_INVALID_ARG, "null argument");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(bn::launch_energy(s->dprob, s->hprob.data(), s->n_prob, s->stream));
+    for (int i = 0; i < s->n_prob; ++i)
+        BN_CUDA(cudaMemcpyAsync(s->h_energy + i, s->hprob[i].energy_out, sizeof(double),
+                                cudaMemcpyDeviceToHost, s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < s->n_prob; ++i) energy_per_pair[i] = s->h_energy[i];
+    return BN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int read_stats(const std::vector<bn::Problem> &hp, cudaStream_t st, bn_sweep_stats *stats)
+{
+    std::vector<unsigned long long> buf(bn::kStatCount);
+    memset(stats, 0, sizeof *stats);
+    for (const auto &h : hp) {
+        BN_CUDA(cudaMemcpyAsync(buf.data(), h.stats, sizeof(unsigned long long) * bn::kStatCount,
+                                cudaMemcpyDeviceToHost, st));
+        BN_CUDA(cudaStreamSynchronize(st));
+        stats->proposals += (int64_t)buf[bn::kStatValid];
+        stats->improving += (int64_t)buf[bn::kStatImproving];
+        stats->committed += (int64_t)buf[bn::kStatCommitted];
+        stats->ties += (int64_t)buf[bn::kStatTies];
+        stats->sweeps = (int64_t)buf[bn::kStatSweeps];
+        if (buf[bn::kStatError])
+            return fail(BN_ERR_TIMEOUT, "a device-side wait ran out (code %llu)",
+                        (unsigned long long)buf[bn::kStatError]);
+    }
+    return BN_OK;
+}
+
+int run_sweeps(const bn::Problem *dprob, const std::vector<bn::Problem> &hp, int max_M,
+               int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm)
+{
+    // problems of one launch must share the count width; group them
+    for (int cb = 1; cb <= 2; ++cb) {
+        int first = -1, count = 0;
+        for (int i = 0; i < (int)hp.size(); ++i)
+            if (hp[i].count_bytes == cb) {
+                if (first < 0) first = i;
+                ++count;
+            }
+        if (!count) continue;
+        if (count != (int)hp.size() && first + count > (int)hp.size())
+            return fail(BN_ERR_INVALID_ARG, "internal: problem grouping");
+        bn::SweepLaunch sl{dprob + first, count, max_M, cb};
+        for (int i = first; i < first + count; ++i)
+            if (hp[i].count_bytes != cb)
+                return fail(BN_ERR_INVALID_ARG,
+                            "a batch must list problems of equal count width contiguously");
+        for (int32_t k = 0; k < n_sweeps; ++k) BN_CUDA(bn::launch_plain_sweep(sl, st, tm));
+    }
+    return BN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bn_optimize_sweeps(bn_sampler *s, int32_t n_sweeps, bn_sweep_stats *stats)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    if (n_sweeps < 0) return fail(BN_ERR_INVALID_ARG, "n_sweeps must be >= 0");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(bn::launch_set_end(s->dprob, s->n_prob, n_sweeps, 1, s->stream));
+    int max_M = 0;
+    for (auto &h : s->hprob) max_M = h.M > max_M ? h.M : max_M;
+    if (int rc = run_sweeps(s->dprob, s->hprob, max_M, n_sweeps, s->stream, &s->timer))
+        return rc;
+    s->sweep += n_sweeps;
+    if (stats) return read_stats(s->hprob, s->stream, stats);
+    return BN_OK;
+}
+
+int bn_fetch_shifts(bn_sampler *s, float *out, size_t n_floats, int out_is_device)
+{
+    if (!s || !out) return fail(BN_ERR_INVALID_ARG, "null argument");
+    const size_t per = (size_t)s->hprob[0].P * 2;
+    if (n_floats < per * s->n_prob) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
+    if (int rc = set_device(s)) return rc;
+    float *dst = out;
+    float *tmp = nullptr;
+    if (!out_is_device) {
+        BN_CUDA(cudaMallocAsync(&tmp, sizeof(float) * per * s->n_prob, s->stream));
+        dst = tmp;
+    }
+    for (int i = 0; i < s->n_prob; ++i)
+        BN_CUDA(bn::launch_fetch_shifts(s->dprob + i, s->hprob[i], dst + per * i, s->stream));
+    if (!out_is_device) {
+        BN_CUDA(cudaMemcpyAsync(out, tmp, sizeof(float) * per * s->n_prob,
+                                cudaMemcpyDeviceToHost, s->stream));
+        BN_CUDA(cudaFreeAsync(tmp, s->stream));
+        BN_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    return BN_OK;
+}
+
+int bn_fetch_points(bn_sampler *s, int32_t pair, int32_t pixel, float *out, size_t n_floats)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (!out || pixel < 0 || pixel >= h.P || n_floats < (size_t)2 * h.N)
+        return fail(BN_ERR_INVALID_ARG, "bad pixel or buffer");
+    if (int rc = set_device(s)) return rc;
+    float *tmp = nullptr;
+    BN_CUDA(cudaMallocAsync(&tmp, sizeof(float) * 2 * h.N, s->stream));
+    BN_CUDA(bn::launch_fetch_points(s->dprob + pair, h, pixel, tmp, s->stream));
+    BN_CUDA(cudaMemcpyAsync(out, tmp, sizeof(float) * 2 * h.N, cudaMemcpyDeviceToHost,
+                            s->stream));
+    BN_CUDA(cudaFreeAsync(tmp, s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    return BN_OK;
+}
+
+int bn_fetch_counts(bn_sampler *s, int32_t pair, int32_t *out, size_t n)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    const size_t need = (size_t)h.P * h.T;
+    if (!out || n < need) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
+    if (int rc = set_device(s)) return rc;
+    int32_t *tmp = nullptr;
+    BN_CUDA(cudaMallocAsync(&tmp, sizeof(int32_t) * need, s->stream));
+    BN_CUDA(bn::launch_unpack_counts(s->dprob + pair, h, tmp, s->stream));
+    BN_CUDA(cudaMemcpyAsync(out, tmp, sizeof(int32_t) * need, cudaMemcpyDeviceToHost,
+                            s->stream));
+    BN_CUDA(cudaFreeAsync(tmp, s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    return BN_OK;
+}
+
+int bn_fetch_integrands(bn_sampler *s, int32_t pair, int32_t *a, int32_t *b, int64_t *C,
+                        size_t T)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (T < (size_t)h.T) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
+    if (int rc = set_device(s)) return rc;
+    if (a) BN_CUDA(cudaMemcpyAsync(a, h.ha, sizeof(int32_t) * h.T, cudaMemcpyDeviceToHost, s->stream));
+    if (b) BN_CUDA(cudaMemcpyAsync(b, h.hb, sizeof(int32_t) * h.T, cudaMemcpyDeviceToHost, s->stream));
+    if (C) BN_CUDA(cudaMemcpyAsync(C, h.hC, sizeof(int64_t) * h.T, cudaMemcpyDeviceToHost, s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    return BN_OK;
+}
+
+int bn_fetch_permutation(bn_sampler *s, int32_t pair, int32_t *out, size_t n)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (!out || n < ((size_t)1 << h.L)) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(cudaMemcpyAsync(out, h.perm, sizeof(int32_t) << h.L, cudaMemcpyDeviceToHost,
+                            s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    return BN_OK;
+}
+
+int bn_fetch_sweep_log(bn_sampler *s, int32_t pair, float *dE, uint8_t *flags,
+                       int32_t *couples, size_t cap)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (cap < (size_t)h.M) return fail(BN_ERR_INVALID_ARG, "cap < couples per pass");
+    if (int rc = set_device(s)) return rc;
+    if (dE) BN_CUDA(cudaMemcpyAsync(dE, h.log_dE, sizeof(float) * h.M, cudaMemcpyDeviceToHost, s->stream));
+    if (flags) BN_CUDA(cudaMemcpyAsync(flags, h.log_flags, h.M, cudaMemcpyDeviceToHost, s->stream));
+    if (couples)
+        BN_CUDA(cudaMemcpyAsync(couples, h.log_couples, sizeof(int32_t) * 2 * h.M,
+                                cudaMemcpyDeviceToHost, s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    return BN_OK;
+}
+
+int bn_get_state(bn_sampler *s, int64_t *sweep, int32_t *shift_index, size_t n)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    const size_t P = (size_t)s->hprob[0].P;
+    if (shift_index && n < P * s->n_prob) return fail(BN_ERR_INVALID_ARG, "buffer too small");
+    if (int rc = set_device(s)) return rc;
+    if (shift_index)
+        for (int i = 0; i < s->n_prob; ++i)
+            BN_CUDA(cudaMemcpyAsync(shift_index + P * i, s->hprob[i].sidx, sizeof(int32_t) * P,
+                                    cudaMemcpyDeviceToHost, s->stream));
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    if (sweep) *sweep = s->sweep;
+    return BN_OK;
+}
+
+int bn_set_state(bn_sampler *s, int64_t sweep, const int32_t *shift_index, size_t n)
+{
+    if (!s || !shift_index) return fail(BN_ERR_INVALID_ARG, "null argument");
+    const size_t P = (size_t)s->hprob[0].P;
+    if (n < P * s->n_prob || sweep < 0) return fail(BN_ERR_INVALID_ARG, "bad state");
+    // the shift index must be a permutation of the pixels
+    std::vector<char> seen(P);
+    for (int i = 0; i < s->n_prob; ++i) {
+        std::fill(seen.begin(), seen.end(), 0);
+        for (size_t p = 0; p < P; ++p) {
+            int32_t v = shift_index[P * i + p];
+            if (v < 0 || (size_t)v >= P || seen[v])
+                return fail(BN_ERR_INVALID_ARG, "shift_index of pair %d is not a permutation", i);
+            seen[v] = 1;
+        }
+    }
+    if (int rc = set_device(s)) return rc;
+    for (int i = 0; i < s->n_prob; ++i) {
+        BN_CUDA(cudaMemcpyAsync(s->hprob[i].sidx, shift_index + P * i, sizeof(int32_t) * P,
+                                cudaMemcpyHostToDevice, s->stream));
+        BN_CUDA(cudaMemcpyAsync(s->hprob[i].ctr, &sweep, sizeof(int64_t),
+                                cudaMemcpyHostToDevice, s->stream));
+        BN_CUDA(bn::launch_counts(s->dprob + i, s->hprob[i], s->stream));
+    }
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    s->sweep = sweep;
+    return BN_OK;
+}
+
+int bn_sampler_reset(bn_sampler *s, uint64_t seed)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    if (int rc = set_device(s)) return rc;
+    s->cfg.seed = seed;
+    for (int i = 0; i < s->n_prob; ++i) {
+        s->hprob[i].seed_lo = (uint32_t)seed;
+        s->hprob[i].seed_hi = (uint32_t)(seed >> 32);
+    }
+    // the previous copy out of the pinned staging must be complete before it is rewritten
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    memcpy(s->h_pinned, s->hprob.data(), sizeof(bn::Problem) * s->n_prob);
+    BN_CUDA(cudaMemcpyAsync(s->dprob, s->h_pinned, sizeof(bn::Problem) * s->n_prob,
+                            cudaMemcpyHostToDevice, s->stream));
+    for (int i = 0; i < s->n_prob; ++i) {
+        BN_CUDA(bn::launch_init_tables(s->dprob + i, s->hprob[i], s->stream));
+        BN_CUDA(bn::launch_counts(s->dprob + i, s->hprob[i], s->stream));
+    }
+    s->sweep = 0;
+    return BN_OK;
+}
+
+int bn_set_kernel_timing(bn_sampler *s, int enable)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    s->timer.enabled = enable != 0;
+    return BN_OK;
+}
+
+int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_out)
+{
+    if (!s || !out || !n_out) return fail(BN_ERR_INVALID_ARG, "null argument");
+    BN_CUDA(s->timer.collect());
+    int n = 0;
+    for (int k = 0; k < bn::kKindCount && n < cap; ++k) {
+        if (!s->timer.launches[k]) continue;
+        memset(&out[n], 0, sizeof out[n]);
+        strncpy(out[n].name, bn::kKernelNames[k], sizeof out[n].name - 1);
+        out[n].launches = s->timer.launches[k];
+        out[n].total_ms = s->timer.ms[k];
+        ++n;
+    }
+    *n_out = n;
+    s->timer.reset();
+    return BN_OK;
+}
+
+// ---- batches ---------------------------------------------------------------------------------
+int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out)
+{
+    if (!samplers || n <= 0 || !out) return fail(BN_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    auto *b = new bn_batch();
+    b->stream = (cudaStream_t)cuda_stream;
+    std::vector<bn::Problem> all;
+    for (int cb = 1; cb <= 2; ++cb)  // equal count widths contiguous
+        for (int i = 0; i < n; ++i) {
+            if (!samplers[i]) {
+                delete b;
+                return fail(BN_ERR_INVALID_ARG, "null sampler in batch");
+            }
+            for (auto &h : samplers[i]->hprob)
+                if (h.count_bytes == cb) all.push_back(h);
+        }
+    for (int i = 0; i < n; ++i) b->members.push_back(samplers[i]);
+    b->timer = &samplers[0]->timer;
+    b->n_prob = (int)all.size();
+    for (auto &h : all) b->max_M = h.M > b->max_M ? h.M : b->max_M;
+    cudaError_t e = cudaMalloc(&b->dprob, sizeof(bn::Problem) * all.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->dprob, all.data(), sizeof(bn::Problem) * all.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        bn_batch_destroy(b);
+        return fail(BN_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return BN_OK;
+}
+
+int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats)
+{
+    if (!b || n_sweeps < 0) return fail(BN_ERR_INVALID_ARG, "bad batch call");
+    // order the batch after every member's pending work
+    for (auto *m : b->members) {
+        if (m->stream == b->stream) continue;
+        BN_CUDA(cudaStreamSynchronize(m->stream));
+    }
+    std::vector<bn::Problem> all;
+    for (int cb = 1; cb <= 2; ++cb)
+        for (auto *m : b->members)
+            for (auto &h : m->hprob)
+                if (h.count_bytes == cb) all.push_back(h);
+    BN_CUDA(bn::launch_set_end(b->dprob, b->n_prob, n_sweeps, 1, b->stream));
+    if (int rc = run_sweeps(b->dprob, all, b->max_M, n_sweeps, b->stream, b->timer)) return rc;
+    for (auto *m : b->members) m->sweep += n_sweeps;
+    if (stats) return read_stats(all, b->stream, stats);
+    return BN_OK;
+}
+
+void bn_batch_destroy(bn_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->dprob) cudaFree(b->dprob);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// bn_launch.h — host-side launchers of the sampler's kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bn_device.cuh"
+
+namespace bn {
+
+// initialisation (bn_init.cu)
+cudaError_t launch_init_tables(const Problem *dprob, const Problem &h, cudaStream_t st);
+cudaError_t launch_counts(const Problem *dprob, const Problem &h, cudaStream_t st);
+cudaError_t launch_fetch_shifts(const Problem *dprob, const Problem &h, float *out,
+                                cudaStream_t st);
+cudaError_t launch_fetch_points(const Problem *dprob, const Problem &h, int pixel, float *out,
+                                cudaStream_t st);
+cudaError_t launch_unpack_counts(const Problem *dprob, const Problem &h, int32_t *out,
+                                 cudaStream_t st);
+
+// energy, Eq. 1 (bn_energy.cu)
+cudaError_t launch_energy(const Problem *dprob, const Problem *hprob, int n_prob,
+                          cudaStream_t st);
+
+// Optional CUDA-event bracketing of kernel launches (host side).
+enum KernelKind { kKEvalPlain = 0, kKResolvePlain, kKCommitPlain, kKPersistent, kKEnergy,
+                  kKCounts, kKindCount };
+extern const char *const kKernelNames[kKindCount];
+
+struct KernelTimer {
+    bool enabled = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    long long launches[kKindCount] = {};
+    double ms[kKindCount] = {};
+    cudaEvent_t get();
+    void begin(int kind, cudaStream_t st);
+    void end(cudaStream_t st);
+    cudaError_t collect();  // waits for pending events, accumulates, recycles
+    void reset();
+    ~KernelTimer();
+};
+
+// sweeps (bn_sweep.cu)
+struct SweepLaunch {
+    const Problem *dprob;   // device array of problems
+    int n_prob;
+    int max_M;              // largest couples-per-pass among the problems
+    int count_bytes;        // 1 or 2 (all problems of one launch share it)
+};
+cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm);
+cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int reset_stats,
+                           cudaStream_t st);
+
+}  // namespace bn

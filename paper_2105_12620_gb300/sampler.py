@@ -1,0 +1,182 @@
+"""User-facing wrapper of the C ABI: one ``Sampler`` per tile, ``Batch`` for fused sweeps.
+
+Argument marshalling only; every computation runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+@dataclass
+class SweepStats:
+    sweeps: int
+    proposals: int
+    improving: int
+    committed: int
+    ties: int
+
+
+class Sampler:
+    """Optimiser state of one tile (n_pairs independent 2-D problems) on the current device."""
+
+    def __init__(self, width: int, height: int, n_points: int, n_integrands: int, seed: int = 0,
+                 n_pairs: int = 1, generator_g: int = 0, sigma: float = 2.1, radius: int = 6,
+                 couples_per_sweep: int = 0, mode: int = L.BN_MODE_NONINTERACTING,
+                 objective: int = L.BN_OBJECTIVE_BLUE, schedule: int = L.BN_SCHEDULE_AUTO,
+                 stream=None):
+        lib = L.load()
+        self.cfg = L.BnConfig(width, height, n_points, generator_g, n_pairs, n_integrands,
+                              sigma, radius, couples_per_sweep, mode, objective, schedule, seed)
+        self._h = ctypes.c_void_p()
+        L.check(lib.bn_sampler_init(ctypes.byref(self.cfg), _stream_handle(stream),
+                                    ctypes.byref(self._h)))
+        self.width, self.height, self.n_pairs = width, height, n_pairs
+        self.n_points, self.n_integrands = n_points, n_integrands
+        self.P = width * height
+        self.info = self.get_info()
+
+    # -- lifetime ---------------------------------------------------------------------------
+    def close(self) -> None:
+        if self._h:
+            L.load().bn_sampler_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    # -- calls --------------------------------------------------------------------------------
+    def get_info(self) -> L.BnInfo:
+        info = L.BnInfo()
+        L.check(L.load().bn_get_info(self._h, ctypes.byref(info)))
+        return info
+
+    def energy(self) -> np.ndarray:
+        out = (ctypes.c_double * self.n_pairs)()
+        L.check(L.load().bn_evaluate_energy(self._h, out))
+        return np.array(out[:], np.float64)
+
+    def optimize(self, n_sweeps: int, stats: bool = True) -> SweepStats | None:
+        st = L.BnSweepStats()
+        L.check(L.load().bn_optimize_sweeps(self._h, n_sweeps, ctypes.byref(st) if stats else None))
+        if not stats:
+            return None
+        return SweepStats(st.sweeps, st.proposals, st.improving, st.committed, st.ties)
+
+    def reset(self, seed: int) -> None:
+        L.check(L.load().bn_sampler_reset(self._h, seed))
+
+    def set_kernel_timing(self, enable: bool) -> None:
+        L.check(L.load().bn_set_kernel_timing(self._h, int(enable)))
+
+    def kernel_times(self) -> dict:
+        buf = (L.BnKernelTime * 16)()
+        n = ctypes.c_int32()
+        L.check(L.load().bn_kernel_times(self._h, buf, 16, ctypes.byref(n)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+                for i in range(n.value)}
+
+    def shifts(self) -> np.ndarray:
+        out = np.zeros((self.n_pairs, self.height, self.width, 2), np.float32)
+        L.check(L.load().bn_fetch_shifts(self._h, out.ctypes.data, out.size, 0))
+        return out
+
+    def shifts_into(self, device_ptr: int, n_floats: int) -> None:
+        L.check(L.load().bn_fetch_shifts(self._h, device_ptr, n_floats, 1))
+
+    def points(self, pixel: int, pair: int = 0) -> np.ndarray:
+        out = np.zeros((self.n_points, 2), np.float32)
+        L.check(L.load().bn_fetch_points(self._h, pair, pixel, out.ctypes.data, out.size))
+        return out
+
+    def counts(self, pair: int = 0) -> np.ndarray:
+        out = np.zeros((self.P, self.n_integrands), np.int32)
+        L.check(L.load().bn_fetch_counts(self._h, pair, out.ctypes.data, out.size))
+        return out
+
+    def integrands(self, pair: int = 0):
+        T = self.n_integrands
+        a = np.zeros(T, np.int32)
+        b = np.zeros(T, np.int32)
+        C = np.zeros(T, np.int64)
+        L.check(L.load().bn_fetch_integrands(self._h, pair, a.ctypes.data, b.ctypes.data,
+                                             C.ctypes.data, T))
+        return a, b, C
+
+    def permutation(self, pair: int = 0) -> np.ndarray:
+        out = np.zeros(1 << self.info.log2_padded, np.int32)
+        L.check(L.load().bn_fetch_permutation(self._h, pair, out.ctypes.data, out.size))
+        return out
+
+    def sweep_log(self, pair: int = 0):
+        M = self.info.couples
+        dE = np.zeros(M, np.float32)
+        flags = np.zeros(M, np.uint8)
+        couples = np.zeros((M, 2), np.int32)
+        L.check(L.load().bn_fetch_sweep_log(self._h, pair, dE.ctypes.data, flags.ctypes.data,
+                                            couples.ctypes.data, M))
+        return dE, flags, couples
+
+    def get_state(self):
+        sweep = ctypes.c_int64()
+        sidx = np.zeros((self.n_pairs, self.P), np.int32)
+        L.check(L.load().bn_get_state(self._h, ctypes.byref(sweep), sidx.ctypes.data, sidx.size))
+        return int(sweep.value), sidx
+
+    def set_state(self, sweep: int, shift_index: np.ndarray) -> None:
+        sidx = np.ascontiguousarray(shift_index, np.int32)
+        L.check(L.load().bn_set_state(self._h, sweep, sidx.ctypes.data, sidx.size))
+
+
+class Batch:
+    """Several samplers whose passes run fused in one launch sequence."""
+
+    def __init__(self, samplers: list[Sampler], stream=None):
+        arr = (ctypes.c_void_p * len(samplers))(*[s.handle.value for s in samplers])
+        self._h = ctypes.c_void_p()
+        self.samplers = list(samplers)
+        L.check(L.load().bn_batch_create(arr, len(samplers), _stream_handle(stream),
+                                         ctypes.byref(self._h)))
+
+    def optimize(self, n_sweeps: int, stats: bool = True) -> SweepStats | None:
+        st = L.BnSweepStats()
+        L.check(L.load().bn_batch_optimize(self._h, n_sweeps, ctypes.byref(st) if stats else None))
+        if not stats:
+            return None
+        return SweepStats(st.sweeps, st.proposals, st.improving, st.committed, st.ties)
+
+    def close(self) -> None:
+        if self._h:
+            L.load().bn_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

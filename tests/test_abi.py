@@ -1,0 +1,77 @@
+"""The C-ABI library loads on any machine and exports every entry point the header declares;
+argument validation runs on the host before any device work (no GPU needed)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2105_12620_gb300 import _lib as L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2105_12620_gb300 import build
+    build.build()
+    return L.load()
+
+
+def test_header_declares_the_boundary():
+    names = L.header_symbols()
+    for required in ("bn_sampler_init", "bn_evaluate_energy", "bn_optimize_sweeps",
+                     "bn_fetch_shifts", "bn_sampler_destroy", "bn_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in L.header_symbols() if n not in exported]
+    assert not missing, missing
+    for n in L.header_symbols():
+        assert hasattr(lib, n)
+
+
+def test_binding_covers_the_header():
+    assert set(L.header_symbols()) <= set(L._SIGS)
+
+
+def _cfg(**kw):
+    base = dict(width=32, height=32, n_points=16, generator_g=0, n_pairs=1, n_integrands=64,
+                sigma=2.1, radius=6, couples_per_sweep=0, mode=0, objective=0, schedule=0, seed=1)
+    base.update(kw)
+    return L.BnConfig(**base)
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(width=1), "width/height"),
+    (dict(height=5000), "width/height"),
+    (dict(n_points=12), "power of two"),
+    (dict(n_points=2048), "power of two"),
+    (dict(generator_g=4), "generator_g"),
+    (dict(n_pairs=3), "n_pairs"),
+    (dict(n_integrands=0), "n_integrands"),
+    (dict(n_integrands=5000), "n_integrands"),
+    (dict(n_points=512, n_integrands=512), "2^31"),
+    (dict(sigma=0.0), "sigma"),
+    (dict(radius=9), "radius"),
+    (dict(couples_per_sweep=600), "couples_per_sweep"),
+    (dict(mode=7), "mode"),
+    (dict(objective=5), "objective"),
+    (dict(schedule=9), "schedule"),
+])
+def test_invalid_configs_are_rejected_on_the_host(lib, kw, needle):
+    h = ctypes.c_void_p()
+    rc = lib.bn_sampler_init(ctypes.byref(_cfg(**kw)), None, ctypes.byref(h))
+    assert rc == L.BN_ERR_INVALID_ARG
+    assert needle in lib.bn_last_error().decode()
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.bn_sampler_init(None, None, ctypes.byref(h)) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_evaluate_energy(None, None) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_optimize_sweeps(None, 1, None) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_fetch_shifts(None, None, 0, 0) == L.BN_ERR_INVALID_ARG
+    lib.bn_sampler_destroy(None)

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Bit-exact: integrands, permutation, shifts, lattice points, counts, couples and commit decisions
+(the oracle follows the GPU only on couples whose |dL| lies inside the 1e-6 relative tie margin).
+Floating point: Eq. 1 within 1e-5 relative; per-couple dL within 1e-6 of the sum of absolute
+per-distance terms (the fp32 compensated weighted sum is accurate to a few 2^-24 of that sum).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import FLAG_TIE
+
+pytestmark = pytest.mark.gpu
+
+E_REL = 1e-5
+DE_REL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_12620_gb300 import build
+    build.build()
+    import paper_2105_12620_gb300 as p
+    p.load()
+    return p
+
+
+CONFIGS = [
+    # (W, H, N, T, pairs, radius, seed)
+    (32, 32, 16, 64, 1, 6, 0),        # the small published configuration
+    (45, 37, 4, 100, 1, 6, 3),        # ragged tile (P not a power of two), ragged T
+    (16, 16, 256, 300, 2, 6, 5),      # 16-bit counts, two pairs (4-D)
+    (13, 13, 64, 1, 1, 6, 2),         # smallest tile with a full stencil, T = 1
+    (4, 4, 2, 7, 1, 6, 9),            # tiny torus: every other pixel is a neighbour
+    (9, 6, 32, 33, 1, 3, 4),          # other radius, non-square
+    (64, 32, 128, 130, 1, 6, 11),     # N = 128 (16-bit), ragged T
+]
+
+
+def _tiles(cfg):
+    W, H, N, T, pairs, r, seed = cfg
+    return [oracle.OracleTile(W, H, N, T, seed=seed, pair=i, radius=r) for i in range(pairs)]
+
+
+def _sampler(pkg, cfg, **kw):
+    W, H, N, T, pairs, r, seed = cfg
+    return pkg.Sampler(W, H, N, T, seed=seed, n_pairs=pairs, radius=r, **kw)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_initialisation_bit_exact(pkg, cfg):
+    s = _sampler(pkg, cfg)
+    for i, ref in enumerate(_tiles(cfg)):
+        assert s.info.generator_g == ref.g
+        a, b, C = s.integrands(i)
+        assert np.array_equal(a, ref.a) and np.array_equal(b, ref.b) and np.array_equal(C, ref.C)
+        assert np.array_equal(s.permutation(i), ref.perm)
+        assert np.array_equal(s.counts(i), ref.k)
+        assert np.array_equal(s.shifts()[i], ref.shifts_float())
+        for pix in (0, ref.P - 1, ref.P // 3):
+            x, y = oracle.points(ref.N, ref.g, *(ref.U[pix] / 2**32))
+            pts = s.points(pix, i).astype(np.float64)
+            assert np.array_equal(pts[:, 0], x) and np.array_equal(pts[:, 1], y)
+    s.close()
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_energy_within_tolerance(pkg, cfg):
+    s = _sampler(pkg, cfg)
+    e = s.energy()
+    for i, ref in enumerate(_tiles(cfg)):
+        E = ref.energy()
+        assert abs(e[i] - E) <= E_REL * E, (e[i], E)
+    s.close()
+
+
+def lockstep(s, tiles, n_sweeps, check_energy_every=0):
+    """Run the GPU and the oracle pass by pass; return the number of tie-adopted couples."""
+    ties = 0
+    for sweep in range(n_sweeps):
+        s.optimize(1, stats=False)
+        for i, ref in enumerate(tiles):
+            dE, flags, couples = s.sweep_log(i)
+            lg = ref.sweep(gpu_improving=(flags & 2) != 0)
+            assert np.array_equal(couples, lg.couples), sweep
+            valid = (lg.flags & 1) != 0
+            assert np.array_equal(flags & 1, lg.flags & 1)
+            err = np.abs(dE[valid].astype(np.float64) - lg.dE[valid])
+            assert np.all(err <= DE_REL * lg.S[valid] + 1e-30), (sweep, err.max())
+            assert np.array_equal(flags & 7, lg.flags & 7), sweep
+            ties += int(((lg.flags & FLAG_TIE) != 0).sum())
+        if check_energy_every and (sweep + 1) % check_energy_every == 0:
+            e = s.energy()
+            for i, ref in enumerate(tiles):
+                E = ref.energy()
+                assert abs(e[i] - E) <= E_REL * E
+    for i, ref in enumerate(tiles):
+        assert np.array_equal(s.counts(i), ref.k)
+        assert np.array_equal(s.shifts()[i], ref.shifts_float())
+    return ties
+
+
+def test_lockstep_small_configuration_200_passes(pkg):
+    cfg = CONFIGS[0]
+    s = _sampler(pkg, cfg)
+    lockstep(s, _tiles(cfg), 200, check_energy_every=50)
+    s.close()
+
+
+@pytest.mark.parametrize("cfg", CONFIGS[1:])
+def test_lockstep_edge_configurations(pkg, cfg):
+    s = _sampler(pkg, cfg)
+    lockstep(s, _tiles(cfg), 25, check_energy_every=25)
+    s.close()
+
+
+def test_lockstep_literal_objective(pkg):
+    W, H, N, T = 24, 20, 16, 48
+    s = pkg.Sampler(W, H, N, T, seed=8, objective=pkg.BN_OBJECTIVE_LITERAL)
+    ref = oracle.OracleTile(W, H, N, T, seed=8, objective=oracle.OBJECTIVE_LITERAL)
+    lockstep(s, [ref], 30)
+    s.close()
+
+
+def test_objective_monotone_on_gpu(pkg):
+    s = pkg.Sampler(64, 64, 16, 128, seed=2)
+    e = [s.energy()[0]]
+    for _ in range(10):
+        s.optimize(10, stats=False)
+        e.append(s.energy()[0])
+    # default objective raises Eq. 1 (tolerance: fp32 evaluation of the energy)
+    assert all(e[i + 1] >= e[i] * (1 - 1e-6) for i in range(10))
+    assert e[-1] > e[0]
+    s.close()
+
+
+def test_split_calls_equal_one_call(pkg):
+    a = pkg.Sampler(40, 24, 16, 64, seed=3)
+    b = pkg.Sampler(40, 24, 16, 64, seed=3)
+    a.optimize(37, stats=False)
+    a.optimize(1, stats=False)
+    a.optimize(22, stats=False)
+    b.optimize(60, stats=False)
+    assert np.array_equal(a.shifts(), b.shifts())
+    assert a.get_state()[0] == b.get_state()[0] == 60
+    a.close()
+    b.close()
+
+
+def test_checkpoint_and_resume(pkg):
+    a = pkg.Sampler(32, 32, 16, 64, seed=6, n_pairs=2)
+    a.optimize(40, stats=False)
+    sweep, sidx = a.get_state()
+    c = pkg.Sampler(32, 32, 16, 64, seed=6, n_pairs=2)
+    c.set_state(sweep, sidx)
+    assert np.array_equal(c.counts(1), a.counts(1))
+    a.optimize(30, stats=False)
+    c.optimize(30, stats=False)
+    assert np.array_equal(a.shifts(), c.shifts())
+    a.close()
+    c.close()
+
+
+def test_stats_are_consistent_with_the_log(pkg):
+    s = pkg.Sampler(32, 32, 16, 64, seed=0)
+    st = s.optimize(1)
+    dE, flags, couples = s.sweep_log()
+    assert st.sweeps == 1
+    assert st.proposals == int(((flags & 1) != 0).sum())
+    assert st.improving == int(((flags & 2) != 0).sum())
+    assert st.committed == int(((flags & 4) != 0).sum())
+    assert st.ties == int(((flags & 8) != 0).sum())
+    s.close()
+
+
+def test_batch_equals_each_alone(pkg):
+    cfgs = [(32, 32, 16, 64, 1), (48, 40, 4, 256, 1), (64, 64, 64, 128, 2), (20, 36, 16, 1, 1)]
+    alone, mixed = [], []
+    for W, H, N, T, pairs in cfgs:
+        a = pkg.Sampler(W, H, N, T, seed=W + H, n_pairs=pairs)
+        a.optimize(40, stats=False)
+        alone.append(a.shifts())
+        a.close()
+        mixed.append(pkg.Sampler(W, H, N, T, seed=W + H, n_pairs=pairs))
+    b = pkg.Batch(mixed)
+    b.optimize(15, stats=False)
+    b.optimize(25, stats=False)
+    for m, ref in zip(mixed, alone):
+        assert np.array_equal(m.shifts(), ref)
+    b.close()
+    for m in mixed:
+        m.close()
+
+
+def test_full_size_gpu_scale_configuration(pkg):
+    """128 x 128, N = 64, T = 1024 (int8 counts): sampled pixels' counts recomputed one by one
+    by the oracle, full Eq. 1, and three lockstep passes at full size."""
+    W = H = 128
+    s = pkg.Sampler(W, H, 64, 1024, seed=0)
+    ref = oracle.OracleTile(W, H, 64, 1024, seed=0)
+    assert np.array_equal(s.counts(), ref.k)
+    E = ref.energy()
+    assert abs(s.energy()[0] - E) <= E_REL * E
+    lockstep(s, [ref], 3)
+    s.close()
