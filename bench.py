@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the screen-space sampler optimiser on GB300.
+
+Workload (one step): optimise a batch of 128 x 128 tiles, each a rank-1 lattice of N = 64 points
+per pixel scored against T = 1024 random Heavisides (int8 counts), Eq. 1 weight sigma 2.1 with
+radius 6, for 2000 passes of the parallel swap optimiser; the step re-initialises every tile
+from a new seed (shifts, integrands, permutation, counts), runs the passes, evaluates Eq. 1 and
+gathers the optimised shifts.  Inputs are synthetic by construction (random Heavisides, Philox
+shifts), so no dataset is involved.
+
+Metric: move proposals evaluated per second (valid couples whose swap energy was evaluated),
+whole job over all ranks; optimised tiles per second is reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W_TILE = H_TILE = 128
+N_POINTS, T_INTEGRANDS, SIGMA, RADIUS, SWEEPS = 64, 1024, 2.1, 6, 2000
+WORKLOAD = ("128x128 toroidal tile, rank-1 lattice N=64 (Korobov g=19), T=1024 random "
+            "Heavisides (int8 counts), Eq.1 weight exp(-d^2/2.1^2) radius 6, 2000 passes")
+METRIC = "move proposals evaluated/sec"
+UNIT = "proposals/s"
+STENCIL_OFFSETS = 112           # neighbours within radius 6 on a tile >= 13 x 13
+L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
+# nominal int8 dot-product (IDP4A) peak: 152 SMs x 64 IDP4A/clk x 4 MAC x 2.07 GHz
+DP4A_PEAK_TOPS = 152 * 64 * 4 * 2.07e9 / 1e12
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+# ------------------------------------------------------------------------------------------------
+# host-side helpers (no GPU needed; covered by CPU tests)
+# ------------------------------------------------------------------------------------------------
+def tile_seed(rank: int, step: int, tile: int, tiles_per_rank: int) -> int:
+    """Seed of one tile: every rank, step and tile gets its own problem (weak scaling)."""
+    return 1_000_003 * rank + tiles_per_rank * step + tile + 1
+
+
+def proposals_per_tile(sweeps: int = SWEEPS) -> int:
+    P = W_TILE * H_TILE
+    return sweeps * P // 8  # P is a power of two: every couple of every pass is valid
+
+
+def parse_clocks(text: str, gpu_index: int | None = None) -> dict:
+    rows = []
+    for line in text.strip().splitlines():
+        if not line or line.startswith("index"):
+            continue
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            idx = int(f[0])
+            sm = float(f[1].split()[0])
+            smax = float(f[2].split()[0])
+        except ValueError:
+            continue
+        if gpu_index is not None and idx != gpu_index:
+            continue
+        rows.append((sm, smax, f[5:9]))
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    reasons = sorted({REASONS[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+    return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows)}
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="bn_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={SMI_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self, gpu_index: int | None) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        text = open(self.path).read() if self.path and os.path.exists(self.path) else ""
+        if self.path and os.path.exists(self.path):
+            os.unlink(self.path)
+        return parse_clocks(text, gpu_index)
+
+
+def physical_gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+        return int(ids[local_rank])
+    return local_rank
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on the host cores
+# ------------------------------------------------------------------------------------------------
+def oracle_rate(n_sweeps: int, seed: int = 1) -> tuple[float, float, str]:
+    """Proposals/s of the plain C oracle on one tile of the workload (single thread)."""
+    import oracle
+    tile = oracle.OracleTile(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=seed, sigma=SIGMA,
+                             radius=RADIUS)
+    t0 = time.perf_counter()
+    props = 0
+    for _ in range(n_sweeps):
+        lg = tile.sweep()
+        props += int((lg.flags & 1).sum())
+    dt = time.perf_counter() - t0
+    sample = f"one 128x128 tile (N=64, T=1024) after initialisation, {n_sweeps} passes"
+    return props / dt, dt, sample
+
+
+def run_reference(args) -> int:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = 3  # passes per step: a bounded sample of the workload (~2 s of CPU each)
+    import oracle
+    tile = oracle.OracleTile(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=1, sigma=SIGMA,
+                             radius=RADIUS)
+    for _ in range(args.warmup):
+        tile.sweep()
+    times, props = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            props += int((tile.sweep().flags & 1).sum())
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = props / total
+    sample = f"{per_step} passes of one 128x128 tile (N=64, T=1024) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "plain C FP64 oracle, single thread",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def plain_per_tile(pkg, stream, rank, sweeps: int = 500, reps: int = 3) -> dict:
+    """The plain schedule (three launches per pass, one warp per couple) on one tile."""
+    import torch
+    t = pkg.Sampler(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=tile_seed(rank, 99, 0, 1),
+                    sigma=SIGMA, radius=RADIUS, schedule=pkg.BN_SCHEDULE_PLAIN, stream=stream)
+    with torch.cuda.stream(stream):
+        t.optimize(100, stats=False)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            t.optimize(sweeps, stats=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    t.close()
+    props = reps * proposals_per_tile(sweeps)
+    return {"value": props / (ms / 1000.0), "unit": UNIT,
+            "tiles_per_s": props / proposals_per_tile() / (ms / 1000.0),
+            "note": f"1 tile, plain schedule, {reps}x{sweeps} passes (no re-initialisation)"}
+
+
+def run_ours(args) -> int:
+    import torch
+
+    import paper_2105_12620_gb300 as pkg
+    from paper_2105_12620_gb300 import build as pkg_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world and world > 1:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not pkg_build.up_to_date():
+        pkg_build.build()
+    if dist is not None:
+        dist.barrier()
+    pkg.load()
+    from paper_2105_12620_gb300 import _lib as L
+
+    stream = torch.cuda.Stream()
+    B = args.tiles
+    schedule = {"auto": pkg.BN_SCHEDULE_AUTO, "plain": pkg.BN_SCHEDULE_PLAIN,
+                "persistent": pkg.BN_SCHEDULE_PERSISTENT}[args.schedule]
+    tiles = [pkg.Sampler(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=tile_seed(rank, 0, i, B),
+                         sigma=SIGMA, radius=RADIUS, schedule=schedule, stream=stream)
+             for i in range(B)]
+    batch = pkg.Batch(tiles, stream=stream) if B > 1 else None
+    shifts_dev = torch.empty((B, H_TILE, W_TILE, 2), dtype=torch.float32, device="cuda")
+    energy_dev = torch.empty((B,), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(k: int):
+        for i, t in enumerate(tiles):
+            t.reset(tile_seed(rank, k, i, B))
+        if batch is not None:
+            batch.optimize(args.sweeps, stats=False)
+        else:
+            tiles[0].optimize(args.sweeps, stats=False)
+        for i, t in enumerate(tiles):
+            t.energy_into(energy_dev[i:i + 1].data_ptr())
+            t.shifts_into(shifts_dev[i].data_ptr(), shifts_dev[i].numel())
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            flush.zero_()
+            step(k)
+        stream.synchronize()
+        tiles[0].set_kernel_timing(True)
+        tiles[0].kernel_times()
+        launches0 = L.load().bn_launch_counter()
+        clocks = ClockSampler()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clock_info = clocks.stop(physical_gpu_index(local))
+        launches = L.load().bn_launch_counter() - launches0
+        ktimes = tiles[0].kernel_times()
+        tiles[0].set_kernel_timing(False)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        local_ms = sum(step_ms)
+        # end to end through the public API with host buffers (pinned staging inside)
+        e2e_ms = []
+        host_shifts = None
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i, t in enumerate(tiles):
+                t.reset(tile_seed(rank, 10_000 + k, i, B))
+            if batch is not None:
+                batch.optimize(args.sweeps, stats=False)
+            else:
+                tiles[0].optimize(args.sweeps, stats=False)
+            host_shifts = [t.shifts() for t in tiles]
+            host_energy = [t.energy() for t in tiles]
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+        del host_energy
+    total_ms = local_ms
+    e2e_total = sum(e2e_ms)
+    if dist is not None:
+        tt = torch.tensor([local_ms, e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, e2e_total = float(tt[0]), float(tt[1])
+    props_step = B * proposals_per_tile(args.sweeps)
+    value = world * props_step * args.steps / (total_ms / 1000.0)
+    e2e_value = world * props_step * args.steps / (e2e_total / 1000.0)
+
+    # dominant kernel and its roofline
+    dom = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
+    roofline = None
+    if dom:
+        name, (nl, tms) = dom
+        per_prop_ops = 2 * STENCIL_OFFSETS * T_INTEGRANDS
+        # algorithmic int8 multiply-accumulates over the timed region / that kernel's time
+        total_ops = B * args.steps * proposals_per_tile(args.sweeps) * per_prop_ops
+        achieved = total_ops / (tms / 1000.0) / 1e12
+        roofline = {"kernel": name, "bound": "alu", "achieved": achieved,
+                    "peak": DP4A_PEAK_TOPS, "unit": "TOP/s", "frac": achieved / DP4A_PEAK_TOPS,
+                    "traffic": None,
+                    "note": "op = one int8 multiply-accumulate; peak = IDP4A nominal "
+                            "(152 SMs x 64/clk x 4 x 2.07 GHz)",
+                    "launches": nl, "avg_launch_ms": tms / nl,
+                    "share": tms / max(sum(v[1] for v in ktimes.values()), 1e-9)}
+    plain = None
+    if not args.no_plain and rank == 0:
+        plain = plain_per_tile(pkg, stream, rank)
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, secs, sample = oracle_rate(args.cpu_sweeps)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                   "seconds": secs}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tiles_per_gpu": B, "sweeps": args.sweeps,
+                       "schedule": args.schedule, "parallelism": f"independent tiles x{world}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "tiles_per_s": world * B * args.steps / (total_ms / 1000.0),
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": B * int(tiles[0].info.reset_h2d_bytes),
+                    "d2h_bytes_per_step": B * (W_TILE * H_TILE * 2 * 4 + 8)},
+            "gpu_launches": int(launches),
+            "clocks": {k: clock_info[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "roofline": roofline,
+            "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in ktimes.items()},
+            "cpu_baseline": cpu,
+            "plain_per_tile": plain,
+        }
+        print(json.dumps(line), flush=True)
+    if batch is not None:
+        batch.close()
+    for t in tiles:
+        t.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tiles", type=int, default=16, help="tiles per GPU per step")
+    ap.add_argument("--sweeps", type=int, default=SWEEPS)
+    ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto")
+    ap.add_argument("--cpu-sweeps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

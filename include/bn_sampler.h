@@ -99,6 +99,7 @@ typedef struct bn_info {
     int32_t schedule;        /* schedule that optimize_sweeps will use                       */
     int64_t sweep;           /* passes done so far (per pair)                                */
     int64_t device_bytes;    /* device memory held by the sampler                            */
+    int64_t reset_h2d_bytes; /* host->device bytes copied by bn_sampler_reset                */
 } bn_info;
 
 typedef struct bn_sampler bn_sampler;
@@ -113,6 +114,9 @@ int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out);
  * over ordered pairs, distances on the torus.  Exact integer sums per squared distance, then
  * an fp32 compensated weighted sum.  energy_per_pair: host, n_pairs doubles.  Synchronises. */
 int bn_evaluate_energy(bn_sampler *s, double *energy_per_pair);
+
+/* Same as bn_evaluate_energy, enqueued only: writes n_pairs doubles to device memory. */
+int bn_evaluate_energy_device(bn_sampler *s, double *energy_per_pair_device);
 
 /* Run n_sweeps passes of the parallel swap optimiser (Sec. 3.4) on every pair; the pass
  * counter persists, so two calls of a and b passes equal one call of a + b.  stats: host,
@@ -166,6 +170,9 @@ int bn_fetch_sweep_log(bn_sampler *s, int32_t pair, float *dE, uint8_t *flags,
 int bn_get_state(bn_sampler *s, int64_t *sweep, int32_t *shift_index, size_t n);
 int bn_set_state(bn_sampler *s, int64_t sweep, const int32_t *shift_index, size_t n);
 
+/* Number of kernels this library has launched in this process (all samplers). */
+int64_t bn_launch_counter(void);
+
 /* ---- kernel timing ------------------------------------------------------------------------ */
 /* When enabled, every sweep kernel launched for this sampler (or a batch containing it) is
  * bracketed by CUDA events on its stream; bn_kernel_times then returns, per kernel name, the
@@ -179,6 +186,21 @@ typedef struct bn_kernel_time {
 int bn_set_kernel_timing(bn_sampler *s, int enable);
 int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_out);
 
+/* ---- execution schedule (speed only; results do not depend on it) ------------------------ */
+/* kind: BN_SCHEDULE_*.  For the persistent kernel, block_x x block_y pixels per work unit,
+ * threads per CTA and proposed pixels per warp per round must name an instantiated shape
+ * (16x8/512/4, 8x8/256/4, 16x8/1024/2); tsplit = chunk ranges per block (1..4, 0 = auto).
+ * block_x = 0 keeps the default shape.  set synchronises the stream. */
+typedef struct bn_schedule {
+    int32_t kind;
+    int32_t block_x, block_y;
+    int32_t threads;
+    int32_t slots_per_warp;
+    int32_t tsplit;
+} bn_schedule;
+int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc);
+int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out);
+
 /* ---- batches: many samplers swept together in one launch sequence ------------------------- */
 typedef struct bn_batch bn_batch;
 
@@ -187,6 +209,8 @@ typedef struct bn_batch bn_batch;
  * (cuda_stream) and records events to order itself after each member's stream. */
 int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out);
 int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats);
+int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc);
+int bn_batch_get_schedule(bn_batch *b, bn_schedule *out);
 void bn_batch_destroy(bn_batch *b);
 
 #ifdef __cplusplus

@@ -26,6 +26,8 @@ TIE_REL = 1e-6
 # +1: reduce Eq. 1 as printed; -1: raise Eq. 1 (= lower the weighted neighbour correlation of
 # the estimates, which yields the blue-noise error of Sec. 3.3).  -1 is the default reading.
 OBJECTIVE_LITERAL, OBJECTIVE_BLUE = 1, -1
+# commit rule: keep only non-interacting improving couples, or every improving couple
+MODE_NONINTERACTING, MODE_CONCURRENT = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -82,8 +84,8 @@ def _declare(L):
     L.bno_sweep_couples.argtypes = [_u64, _i32, _u32, _i32, _i32, _i32p, _i32p]
     L.bno_priority_key.argtypes = [_u64, _i32, _u32, _i32]
     L.bno_priority_key.restype = _u64
-    L.bno_sweep.argtypes = [_i32, _i32, _i32, _i32, _f64, _i32, _i32, _u64, _i32, _u32, _i32,
-                            _i32,
+    L.bno_sweep.argtypes = [_i32, _i32, _i32, _i32, _f64, _i32, _i32, _i32, _u64, _i32, _u32,
+                            _i32, _i32,
                             _i32p, _i32p, _i32p, ctypes.c_void_p, _f64, _f64p, _f64p,
                             _u8p, _i32p]
     L.bno_sweep.restype = _i32
@@ -200,13 +202,15 @@ class OracleTile:
     """State of one 2-D pair: shifts, estimate counts, shift index, candidate permutation."""
 
     def __init__(self, width, height, n_points, n_integrands, seed, pair=0, generator_g=0,
-                 sigma=2.1, radius=6, couples_per_sweep=0, objective=OBJECTIVE_BLUE):
+                 sigma=2.1, radius=6, couples_per_sweep=0, objective=OBJECTIVE_BLUE,
+                 mode=MODE_NONINTERACTING):
         self.W, self.H, self.N, self.T = width, height, n_points, n_integrands
         self.P = width * height
         self.L = log2_ceil(self.P)
         self.seed, self.pair = seed, pair
         self.sigma, self.r = sigma, radius
         self.objective = objective
+        self.mode = mode
         self.g = generator_g if generator_g else pick_g(n_points)
         self.M = couples_per_sweep if couples_per_sweep else (1 << self.L) // 8
         self.U = shifts(seed, pair, self.P)
@@ -235,7 +239,8 @@ class OracleTile:
             gi = np.ascontiguousarray(gpu_improving, np.uint8)
             ptr = gi.ctypes.data
         committed = lib().bno_sweep(self.W, self.H, self.N, self.T, self.sigma, self.r,
-                                    self.objective, self.seed, self.pair, self.sweep_index,
+                                    self.objective, self.mode, self.seed, self.pair,
+                                    self.sweep_index,
                                     self.L, M,
                                     self.perm, self.k, self.sidx, ptr, tie_rel, dE, S, flags,
                                     couples)

@@ -375,6 +375,9 @@ double bno_delta_energy(int32_t W, int32_t H, int32_t N, int32_t T, const int32_
  *      priority (Philox draw, then lower j) is kept, so the kept changes add up exactly.
  *   5. The kept swaps are applied to the estimate vectors and the shift index of the tile.
  * dE[j] is the change of Eq. 1 (not of the objective); improving means objective * dE < 0.
+ * mode = 1 (concurrent) keeps every improving couple, with no interaction filter: this is the
+ * paper's own GPU optimiser, whose loss can move the wrong way while many neighbouring swaps
+ * land in the same pass.
  * Lockstep use: if gpu_improving is given, couples whose |dE| is below tie_rel * S_j (S_j = sum
  * of the absolute per-distance changes) take their improving flag from it instead; such
  * couples are flagged in flags bit 3.
@@ -408,7 +411,7 @@ uint64_t bno_priority_key(uint64_t seed, int32_t pair, uint32_t sweep, int32_t j
 }
 
 int32_t bno_sweep(int32_t W, int32_t H, int32_t N, int32_t T, double sigma, int32_t r,
-                  int32_t objective, uint64_t seed, int32_t pair, uint32_t sweep, int32_t L,
+                  int32_t objective, int32_t mode, uint64_t seed, int32_t pair, uint32_t sweep, int32_t L,
                   int32_t M, const int32_t *perm, int32_t *k /* [P][T] in/out */,
                   int32_t *sidx /* [P] in/out */, const uint8_t *gpu_improving /* [M] or NULL */,
                   double tie_rel, double *dE /* [M] */, double *S /* [M] */,
@@ -438,6 +441,10 @@ int32_t bno_sweep(int32_t W, int32_t H, int32_t N, int32_t T, double sigma, int3
     int32_t committed = 0;
     for (int32_t j = 0; j < M; ++j) {
         if (!(flags[j] & 2)) continue;
+        if (mode == 1) {
+            flags[j] |= 4;
+            continue;
+        }
         uint64_t kj = bno_priority_key(seed, pair, sweep, j);
         int wins = 1;
         for (int32_t i = 0; i < M && wins; ++i) {

@@ -45,12 +45,23 @@ class BnInfo(ctypes.Structure):
                 ("couples", ctypes.c_int32), ("count_bytes", ctypes.c_int32),
                 ("row_bytes", ctypes.c_int32), ("n_offsets", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("sweep", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("sweep", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("reset_h2d_bytes", ctypes.c_int64)]
 
 
 class BnKernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double)]
+
+
+class BnSchedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("block_x", ctypes.c_int32),
+                ("block_y", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("slots_per_warp", ctypes.c_int32), ("tsplit", ctypes.c_int32)]
+
+
+# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, slots/warp)
+PERSISTENT_SHAPES = [(16, 8, 512, 4), (8, 8, 256, 4), (16, 8, 1024, 2)]
 
 
 class BnError(RuntimeError):
@@ -75,10 +86,16 @@ _SIGS = {
     "bn_fetch_sweep_log": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t]),
     "bn_get_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _P, ctypes.c_size_t]),
     "bn_set_state": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_size_t]),
+    "bn_evaluate_energy_device": (ctypes.c_int, [_P, _P]),
+    "bn_launch_counter": (ctypes.c_int64, []),
     "bn_sampler_reset": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "bn_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "bn_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(BnKernelTime), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]),
+    "bn_sampler_set_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
+    "bn_sampler_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
+    "bn_batch_set_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
+    "bn_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
     "bn_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P,
                                        ctypes.POINTER(_P)]),
     "bn_batch_optimize": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSweepStats)]),
@@ -91,7 +108,7 @@ _lib = None
 def header_symbols() -> list[str]:
     """Names of every entry point declared in include/bn_sampler.h."""
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(bn_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|void|const char \*)\s*\*?\s*(bn_\w+)\s*\(",
                                  text, re.M)))
 
 

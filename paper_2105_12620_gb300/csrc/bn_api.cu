@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bn_launch.h"
+#include "bn_persistent.h"
 #include "bn_sampler.h"
 
 namespace {
@@ -88,6 +89,30 @@ struct Slab {
 
 }  // namespace
 
+namespace {
+
+// How the passes of a set of problems are executed, and the device arrays that go with it.
+struct SweepPlan {
+    bool persistent = false;
+    bn::PersistentShape shape{16, 8, 512, 4, 1};
+    // per count width (index cb - 1): first problem, problem count, units / couples prefix
+    int first[2] = {0, 0}, count[2] = {0, 0};
+    int total_units[2] = {0, 0}, total_couples[2] = {0, 0};
+    int *d_prefix = nullptr;        // [2][2][n_prob + 1] unit / couple prefix sums
+    bn::GridBarrier *d_bar = nullptr;
+    int n_prob = 0, max_M = 0, sms = 0;
+};
+
+void free_plan(SweepPlan &pl)
+{
+    if (pl.d_prefix) cudaFree(pl.d_prefix);
+    if (pl.d_bar) cudaFree(pl.d_bar);
+    pl.d_prefix = nullptr;
+    pl.d_bar = nullptr;
+}
+
+}  // namespace
+
 struct bn_sampler {
     bn_config cfg{};
     cudaStream_t stream = nullptr;
@@ -98,10 +123,13 @@ struct bn_sampler {
     char *slab = nullptr;
     size_t slab_bytes = 0;
     double *h_energy = nullptr;  // pinned, [n_prob]
+    float *d_shifts = nullptr;   // device staging of fetched shifts [n_prob][P][2]
+    float *h_shifts = nullptr;   // pinned staging of fetched shifts
     int64_t sweep = 0;           // host mirror of the pass counter
     int schedule = BN_SCHEDULE_PLAIN;
     bn::Problem *h_pinned = nullptr;  // pinned staging of the descriptors (reset)
     bn::KernelTimer timer;
+    SweepPlan plan;
 };
 
 struct bn_batch {
@@ -112,6 +140,8 @@ struct bn_batch {
     int max_M = 0;
     int count_bytes = 1;
     bn::KernelTimer *timer = nullptr;  // the first member's timer
+    std::vector<bn::Problem> all;      // host copies, grouped by count width
+    SweepPlan plan;
 };
 
 namespace {
@@ -225,9 +255,9 @@ void carve(Slab &s, bn::Problem &h)
     h.hC = s.take<int64_t>(h.T);
     h.owner = s.take<unsigned long long>((size_t)h.P * 2);
     h.log_dE = s.take<float>(h.M);
-    h.log_flags = s.take<uint8_t>(h.M);
+    h.log_flags = s.take<uint8_t>((size_t)h.M + 4);  // phase 2 reads aligned 4-byte words
     h.log_couples = s.take<int32_t>((size_t)h.M * 2);
-    h.side_cls = s.take<int32_t>((size_t)h.M * 2 * bn::kMaxClasses);
+    h.side_cls = s.take<int32_t>((size_t)h.M * 2 * bn::kMaxTsplit * bn::kMaxClasses);
     h.arrivals = s.take<int32_t>(h.M);
     h.ctr = s.take<long long>(4);
     h.stats = s.take<unsigned long long>(bn::kStatCount);
@@ -250,6 +280,115 @@ int set_device(const bn_sampler *s)
     return BN_OK;
 }
 
+// Build the execution plan of a problem list (grouped by count width, 1-byte group first).
+// schedule: BN_SCHEDULE_*; the persistent schedule needs the radius-6 stencil on tiles of at
+// least 13 x 13 for every problem.
+int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int schedule,
+              const bn::PersistentShape *want, SweepPlan &pl)
+{
+    free_plan(pl);
+    pl.n_prob = (int)hp.size();
+    pl.max_M = 0;
+    for (auto &h : hp) pl.max_M = h.M > pl.max_M ? h.M : pl.max_M;
+    int dev = 0;
+    BN_CUDA(cudaGetDevice(&dev));
+    BN_CUDA(cudaDeviceGetAttribute(&pl.sms, cudaDevAttrMultiProcessorCount, dev));
+    bool ok = true;
+    for (auto &h : hp) ok = ok && bn::persistent_supported(h);
+    if (schedule == BN_SCHEDULE_PERSISTENT && !ok)
+        return fail(BN_ERR_INVALID_ARG,
+                    "the persistent schedule needs radius 6 and tiles of at least 13 x 13");
+    pl.persistent = ok && schedule != BN_SCHEDULE_PLAIN;
+    for (int g = 0; g < 2; ++g) {
+        pl.first[g] = pl.count[g] = 0;
+        int f = -1;
+        for (int i = 0; i < pl.n_prob; ++i)
+            if (hp[i].count_bytes == g + 1) {
+                if (f < 0) f = i;
+                ++pl.count[g];
+            }
+        pl.first[g] = f < 0 ? 0 : f;
+        for (int i = pl.first[g]; i < pl.first[g] + pl.count[g]; ++i)
+            if (hp[i].count_bytes != g + 1)
+                return fail(BN_ERR_INVALID_ARG, "internal: problems not grouped by count width");
+    }
+    if (!pl.persistent) return BN_OK;
+    if (want) pl.shape = *want;
+    // default chunk split: enough work units to cover every SM twice
+    int units1 = 0, min_chunks = 1 << 30;
+    for (auto &h : hp) {
+        units1 += bn::persistent_units_per_problem(h, pl.shape.bx, pl.shape.by, 1);
+        const int nc = h.row_bytes / 128;
+        min_chunks = nc < min_chunks ? nc : min_chunks;
+    }
+    if (!want || pl.shape.tsplit <= 0) {
+        int ts = (2 * pl.sms + units1 - 1) / units1;
+        pl.shape.tsplit = ts;
+    }
+    if (pl.shape.tsplit > bn::kMaxTsplit) pl.shape.tsplit = bn::kMaxTsplit;
+    if (pl.shape.tsplit > min_chunks) pl.shape.tsplit = min_chunks;
+    if (pl.shape.tsplit < 1) pl.shape.tsplit = 1;
+    std::vector<int> pre((size_t)4 * (pl.n_prob + 1), 0);
+    for (int g = 0; g < 2; ++g) {
+        int *us = pre.data() + (size_t)(2 * g) * (pl.n_prob + 1);
+        int *cs = pre.data() + (size_t)(2 * g + 1) * (pl.n_prob + 1);
+        for (int k = 0; k < pl.count[g]; ++k) {
+            const bn::Problem &h = hp[pl.first[g] + k];
+            us[k + 1] = us[k] + bn::persistent_units_per_problem(h, pl.shape.bx, pl.shape.by,
+                                                                 pl.shape.tsplit);
+            cs[k + 1] = cs[k] + h.M;
+        }
+        pl.total_units[g] = us[pl.count[g]];
+        pl.total_couples[g] = cs[pl.count[g]];
+    }
+    BN_CUDA(cudaMalloc(&pl.d_prefix, sizeof(int) * pre.size()));
+    BN_CUDA(cudaMemcpy(pl.d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
+    BN_CUDA(cudaMalloc(&pl.d_bar, sizeof(bn::GridBarrier)));
+    (void)dprob;
+    return BN_OK;
+}
+
+constexpr int kItersPerLaunch = 500;
+
+int run_plan(const SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Problem> &hp,
+             int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm)
+{
+    BN_CUDA(bn::launch_set_end(dprob, pl.n_prob, n_sweeps, 1, st));
+    if (!pl.persistent) {
+        for (int g = 0; g < 2; ++g) {
+            if (!pl.count[g]) continue;
+            bn::SweepLaunch sl{dprob + pl.first[g], pl.count[g], pl.max_M, g + 1};
+            for (int32_t k = 0; k < n_sweeps; ++k) BN_CUDA(bn::launch_plain_sweep(sl, st, tm));
+        }
+        return BN_OK;
+    }
+    for (int g = 0; g < 2; ++g) {
+        if (!pl.count[g]) continue;
+        bn::PersistentArgs a{};
+        a.probs = dprob + pl.first[g];
+        a.n_prob = pl.count[g];
+        a.unit_start = pl.d_prefix + (size_t)(2 * g) * (pl.n_prob + 1);
+        a.couple_start = pl.d_prefix + (size_t)(2 * g + 1) * (pl.n_prob + 1);
+        a.total_units = pl.total_units[g];
+        a.total_couples = pl.total_couples[g];
+        a.tsplit = pl.shape.tsplit;
+        a.bar = pl.d_bar;
+        for (int32_t done = 0; done < n_sweeps; done += kItersPerLaunch) {
+            a.n_iter = n_sweeps - done < kItersPerLaunch ? n_sweeps - done : kItersPerLaunch;
+            BN_CUDA(cudaMemsetAsync(pl.d_bar, 0, sizeof(bn::GridBarrier), st));
+            const bool timed = tm && tm->enabled;
+            if (timed) tm->begin(bn::kKPersistent, st);
+            cudaError_t e = bn::launch_persistent(a, pl.shape, g + 1, pl.sms, st);
+            if (timed) tm->end(st);
+            if (e != cudaSuccess)
+                return fail(BN_ERR_CUDA, "persistent launch (%dx%d, %d threads) failed: %s",
+                            pl.shape.bx, pl.shape.by, pl.shape.threads, cudaGetErrorString(e));
+        }
+    }
+    (void)hp;
+    return BN_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -269,8 +408,6 @@ int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
     s->cfg = *cfg;
     s->stream = (cudaStream_t)cuda_stream;
     s->n_prob = cfg->n_pairs;
-    s->schedule = cfg->schedule == BN_SCHEDULE_PERSISTENT ? BN_SCHEDULE_PERSISTENT
-                                                          : BN_SCHEDULE_PLAIN;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return fail(BN_ERR_CUDA, "no CUDA device");
@@ -286,6 +423,9 @@ int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
     if (e == cudaSuccess) e = cudaMalloc(&s->dprob, sizeof(bn::Problem) * s->n_prob);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_energy, sizeof(double) * s->n_prob);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_pinned, sizeof(bn::Problem) * s->n_prob);
+    const size_t shift_floats = (size_t)s->hprob[0].P * 2 * s->n_prob;
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_shifts, sizeof(float) * shift_floats);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_shifts, sizeof(float) * shift_floats);
     if (e != cudaSuccess) {
         bn_sampler_destroy(s);
         cudaGetLastError();
@@ -308,6 +448,12 @@ int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
         bn_sampler_destroy(s);
         return fail(BN_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
     }
+    if (int rc2 = make_plan(s->hprob, s->dprob, cfg->schedule, nullptr, s->plan)) {
+        std::string msg = g_error;
+        bn_sampler_destroy(s);
+        return fail(rc2, "%s", msg.c_str());
+    }
+    s->schedule = s->plan.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
     *out = s;
     return BN_OK;
 }
@@ -320,6 +466,9 @@ void bn_sampler_destroy(bn_sampler *s)
     if (s->dprob) cudaFree(s->dprob);
     if (s->h_energy) cudaFreeHost(s->h_energy);
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    if (s->d_shifts) cudaFree(s->d_shifts);
+    if (s->h_shifts) cudaFreeHost(s->h_shifts);
+    free_plan(s->plan);
     delete s;
 }
 
@@ -337,6 +486,7 @@ int bn_get_info(bn_sampler *s, bn_info *info)
     info->schedule = s->schedule;
     info->sweep = s->sweep;
     info->device_bytes = (int64_t)s->slab_bytes;
+    info->reset_h2d_bytes = (int64_t)(sizeof(bn::Problem) * s->n_prob);
     return BN_OK;
 }
 
@@ -352,6 +502,17 @@ int bn_evaluate_energy(bn_sampler *s, double *energy_per_pair)
     for (int i = 0; i < s->n_prob; ++i) energy_per_pair[i] = s->h_energy[i];
     return BN_OK;
 }
+
+int bn_evaluate_energy_device(bn_sampler *s, double *energy_per_pair_device)
+{
+    if (!s || !energy_per_pair_device) return fail(BN_ERR_INVALID_ARG, "null argument");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(bn::launch_energy(s->dprob, s->hprob.data(), s->n_prob, s->stream));
+    BN_CUDA(bn::launch_energy_copy(s->dprob, s->n_prob, energy_per_pair_device, s->stream));
+    return BN_OK;
+}
+
+int64_t bn_launch_counter(void) { return (int64_t)bn::launch_count(); }
 
 }  // extern "C"
 
@@ -377,30 +538,6 @@ int read_stats(const std::vector<bn::Problem> &hp, cudaStream_t st, bn_sweep_sta
     return BN_OK;
 }
 
-int run_sweeps(const bn::Problem *dprob, const std::vector<bn::Problem> &hp, int max_M,
-               int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm)
-{
-    // problems of one launch must share the count width; group them
-    for (int cb = 1; cb <= 2; ++cb) {
-        int first = -1, count = 0;
-        for (int i = 0; i < (int)hp.size(); ++i)
-            if (hp[i].count_bytes == cb) {
-                if (first < 0) first = i;
-                ++count;
-            }
-        if (!count) continue;
-        if (count != (int)hp.size() && first + count > (int)hp.size())
-            return fail(BN_ERR_INVALID_ARG, "internal: problem grouping");
-        bn::SweepLaunch sl{dprob + first, count, max_M, cb};
-        for (int i = first; i < first + count; ++i)
-            if (hp[i].count_bytes != cb)
-                return fail(BN_ERR_INVALID_ARG,
-                            "a batch must list problems of equal count width contiguously");
-        for (int32_t k = 0; k < n_sweeps; ++k) BN_CUDA(bn::launch_plain_sweep(sl, st, tm));
-    }
-    return BN_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -410,11 +547,7 @@ int bn_optimize_sweeps(bn_sampler *s, int32_t n_sweeps, bn_sweep_stats *stats)
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
     if (n_sweeps < 0) return fail(BN_ERR_INVALID_ARG, "n_sweeps must be >= 0");
     if (int rc = set_device(s)) return rc;
-    BN_CUDA(bn::launch_set_end(s->dprob, s->n_prob, n_sweeps, 1, s->stream));
-    int max_M = 0;
-    for (auto &h : s->hprob) max_M = h.M > max_M ? h.M : max_M;
-    if (int rc = run_sweeps(s->dprob, s->hprob, max_M, n_sweeps, s->stream, &s->timer))
-        return rc;
+    if (int rc = run_plan(s->plan, s->dprob, s->hprob, n_sweeps, s->stream, &s->timer)) return rc;
     s->sweep += n_sweeps;
     if (stats) return read_stats(s->hprob, s->stream, stats);
     return BN_OK;
@@ -426,19 +559,14 @@ int bn_fetch_shifts(bn_sampler *s, float *out, size_t n_floats, int out_is_devic
     const size_t per = (size_t)s->hprob[0].P * 2;
     if (n_floats < per * s->n_prob) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
     if (int rc = set_device(s)) return rc;
-    float *dst = out;
-    float *tmp = nullptr;
-    if (!out_is_device) {
-        BN_CUDA(cudaMallocAsync(&tmp, sizeof(float) * per * s->n_prob, s->stream));
-        dst = tmp;
-    }
+    float *dst = out_is_device ? out : s->d_shifts;
     for (int i = 0; i < s->n_prob; ++i)
         BN_CUDA(bn::launch_fetch_shifts(s->dprob + i, s->hprob[i], dst + per * i, s->stream));
     if (!out_is_device) {
-        BN_CUDA(cudaMemcpyAsync(out, tmp, sizeof(float) * per * s->n_prob,
+        BN_CUDA(cudaMemcpyAsync(s->h_shifts, s->d_shifts, sizeof(float) * per * s->n_prob,
                                 cudaMemcpyDeviceToHost, s->stream));
-        BN_CUDA(cudaFreeAsync(tmp, s->stream));
         BN_CUDA(cudaStreamSynchronize(s->stream));
+        memcpy(out, s->h_shifts, sizeof(float) * per * s->n_prob);
     }
     return BN_OK;
 }
@@ -610,6 +738,68 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
     return BN_OK;
 }
 
+static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Problem *dprob,
+                               const bn_schedule *sc, SweepPlan &plan)
+{
+    if (!sc) return fail(BN_ERR_INVALID_ARG, "null schedule");
+    if (sc->kind != BN_SCHEDULE_PLAIN && sc->kind != BN_SCHEDULE_PERSISTENT &&
+        sc->kind != BN_SCHEDULE_AUTO)
+        return fail(BN_ERR_INVALID_ARG, "unknown schedule kind %d", sc->kind);
+    bn::PersistentShape shape{sc->block_x, sc->block_y, sc->threads, sc->slots_per_warp,
+                              sc->tsplit};
+    bool known = false;
+#define BN_KNOWN(BX, BY, NT, SPW, MINB)                                                       \
+    known = known || (shape.bx == BX && shape.by == BY && shape.threads == NT && shape.spw == SPW);
+    BN_PERSISTENT_SHAPES(BN_KNOWN)
+#undef BN_KNOWN
+    const bool want_shape = sc->kind != BN_SCHEDULE_PLAIN && sc->block_x > 0;
+    if (want_shape && !known)
+        return fail(BN_ERR_INVALID_ARG, "no kernel instantiated for block %dx%d, %d threads, %d "
+                    "slots per warp", sc->block_x, sc->block_y, sc->threads, sc->slots_per_warp);
+    return make_plan(hp, dprob, sc->kind, want_shape ? &shape : nullptr, plan);
+}
+
+static void get_schedule_common(const SweepPlan &pl, bn_schedule *out)
+{
+    out->kind = pl.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    out->block_x = pl.shape.bx;
+    out->block_y = pl.shape.by;
+    out->threads = pl.shape.threads;
+    out->slots_per_warp = pl.shape.spw;
+    out->tsplit = pl.shape.tsplit;
+}
+
+int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    if (int rc = set_schedule_common(s->hprob, s->dprob, sc, s->plan)) return rc;
+    s->schedule = s->plan.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    return BN_OK;
+}
+
+int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out)
+{
+    if (!s || !out) return fail(BN_ERR_INVALID_ARG, "null argument");
+    get_schedule_common(s->plan, out);
+    return BN_OK;
+}
+
+int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc)
+{
+    if (!b) return fail(BN_ERR_INVALID_ARG, "null batch");
+    BN_CUDA(cudaStreamSynchronize(b->stream));
+    return set_schedule_common(b->all, b->dprob, sc, b->plan);
+}
+
+int bn_batch_get_schedule(bn_batch *b, bn_schedule *out)
+{
+    if (!b || !out) return fail(BN_ERR_INVALID_ARG, "null argument");
+    get_schedule_common(b->plan, out);
+    return BN_OK;
+}
+
 // ---- batches ---------------------------------------------------------------------------------
 int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out)
 {
@@ -639,6 +829,15 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
         bn_batch_destroy(b);
         return fail(BN_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
     }
+    int sched = BN_SCHEDULE_AUTO;
+    for (int i = 0; i < n; ++i)
+        if (samplers[i]->cfg.schedule == BN_SCHEDULE_PLAIN) sched = BN_SCHEDULE_PLAIN;
+    b->all = all;
+    if (int rc = make_plan(b->all, b->dprob, sched, nullptr, b->plan)) {
+        std::string msg = g_error;
+        bn_batch_destroy(b);
+        return fail(rc, "%s", msg.c_str());
+    }
     *out = b;
     return BN_OK;
 }
@@ -651,15 +850,9 @@ int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats)
         if (m->stream == b->stream) continue;
         BN_CUDA(cudaStreamSynchronize(m->stream));
     }
-    std::vector<bn::Problem> all;
-    for (int cb = 1; cb <= 2; ++cb)
-        for (auto *m : b->members)
-            for (auto &h : m->hprob)
-                if (h.count_bytes == cb) all.push_back(h);
-    BN_CUDA(bn::launch_set_end(b->dprob, b->n_prob, n_sweeps, 1, b->stream));
-    if (int rc = run_sweeps(b->dprob, all, b->max_M, n_sweeps, b->stream, b->timer)) return rc;
+    if (int rc = run_plan(b->plan, b->dprob, b->all, n_sweeps, b->stream, b->timer)) return rc;
     for (auto *m : b->members) m->sweep += n_sweeps;
-    if (stats) return read_stats(all, b->stream, stats);
+    if (stats) return read_stats(b->all, b->stream, stats);
     return BN_OK;
 }
 
@@ -668,6 +861,7 @@ void bn_batch_destroy(bn_batch *b)
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     if (b->dprob) cudaFree(b->dprob);
+    free_plan(b->plan);
     delete b;
 }
 

@@ -95,6 +95,22 @@ cudaError_t launch_energy(const Problem *dprob, const Problem *hprob, int n_prob
     else
         k_energy<2><<<grid, kEnergyThreads, 0, st>>>(dprob);
     k_energy_finalize<<<n_prob, 32, 0, st>>>(dprob);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_energy_copy(const Problem *probs, double *out)
+{
+    out[blockIdx.x] = *probs[blockIdx.x].energy_out;
+}
+}  // namespace
+
+cudaError_t launch_energy_copy(const Problem *dprob, int n_prob, double *dev_out,
+                               cudaStream_t st)
+{
+    k_energy_copy<<<n_prob, 1, 0, st>>>(dprob, dev_out);
+    note_launches(1);
     return cudaGetLastError();
 }
 

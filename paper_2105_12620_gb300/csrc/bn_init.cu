@@ -1,5 +1,7 @@
 // bn_init.cu — initialisation kernels: shifts, Heaviside bank, candidate permutation and the
 // counting kernel (test-integrand estimates of every pixel), plus fetch helpers.
+#include <atomic>
+
 #include "bn_launch.h"
 
 namespace bn {
@@ -149,7 +151,12 @@ __global__ void k_unpack_counts(const Problem *probs, int32_t *out)
 
 int perm_rounds(int L) { return 6 * L < 12 ? 12 : 6 * L; }
 
+std::atomic<long long> g_launches{0};
+
 }  // namespace
+
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_init_tables(const Problem *dprob, const Problem &h, cudaStream_t st)
 {
@@ -159,6 +166,7 @@ cudaError_t launch_init_tables(const Problem *dprob, const Problem &h, cudaStrea
     k_init_perm<<<((1 << h.L) + nt - 1) / nt, nt, 0, st>>>(dprob, perm_rounds(h.L));
     const int nclear = 2 * h.P > h.M ? 2 * h.P : h.M;
     k_clear_state<<<(nclear + nt - 1) / nt, nt, 0, st>>>(dprob);
+    note_launches(4);
     return cudaGetLastError();
 }
 
@@ -172,6 +180,7 @@ cudaError_t launch_counts(const Problem *dprob, const Problem &h, cudaStream_t s
         k_counts<uint8_t><<<grid, kCountThreads, smem, st>>>(dprob);
     else
         k_counts<uint16_t><<<grid, kCountThreads, smem, st>>>(dprob);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -179,6 +188,7 @@ cudaError_t launch_fetch_shifts(const Problem *dprob, const Problem &h, float *o
                                 cudaStream_t st)
 {
     k_fetch_shifts<<<(h.P + 255) / 256, 256, 0, st>>>(dprob, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -186,6 +196,7 @@ cudaError_t launch_fetch_points(const Problem *dprob, const Problem &h, int pixe
                                 cudaStream_t st)
 {
     k_fetch_points<<<(h.N + 255) / 256, 256, 0, st>>>(dprob, pixel, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -198,6 +209,7 @@ cudaError_t launch_unpack_counts(const Problem *dprob, const Problem &h, int32_t
         k_unpack_counts<uint8_t><<<blocks, 256, 0, st>>>(dprob, out);
     else
         k_unpack_counts<uint16_t><<<blocks, 256, 0, st>>>(dprob, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 

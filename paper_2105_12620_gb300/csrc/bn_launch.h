@@ -10,6 +10,10 @@
 
 namespace bn {
 
+// process-wide count of kernel launches made by this library
+void note_launches(long long n);
+long long launch_count();
+
 // initialisation (bn_init.cu)
 cudaError_t launch_init_tables(const Problem *dprob, const Problem &h, cudaStream_t st);
 cudaError_t launch_counts(const Problem *dprob, const Problem &h, cudaStream_t st);
@@ -23,6 +27,8 @@ cudaError_t launch_unpack_counts(const Problem *dprob, const Problem &h, int32_t
 // energy, Eq. 1 (bn_energy.cu)
 cudaError_t launch_energy(const Problem *dprob, const Problem *hprob, int n_prob,
                           cudaStream_t st);
+cudaError_t launch_energy_copy(const Problem *dprob, int n_prob, double *dev_out,
+                               cudaStream_t st);
 
 // Optional CUDA-event bracketing of kernel launches (host side).
 enum KernelKind { kKEvalPlain = 0, kKResolvePlain, kKCommitPlain, kKPersistent, kKEnergy,

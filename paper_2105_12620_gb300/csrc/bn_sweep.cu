@@ -230,6 +230,7 @@ cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int r
                            cudaStream_t st)
 {
     k_set_end<<<n_prob, 32, 0, st>>>(dprob, n_sweeps, reset_stats);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -249,6 +250,7 @@ cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTim
     if (timed) tm->begin(kKCommitPlain, st);
     k_commit_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
     if (timed) tm->end(st);
+    note_launches(3);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,16 @@ class SweepStats:
     ties: int
 
 
+def _schedule(kind, shape=None, tsplit=0) -> L.BnSchedule:
+    bx, by, nt, spw = shape if shape else (0, 0, 0, 0)
+    return L.BnSchedule(kind, bx, by, nt, spw, tsplit)
+
+
+def _unpack(sc: L.BnSchedule) -> dict:
+    return {"kind": sc.kind, "shape": (sc.block_x, sc.block_y, sc.threads, sc.slots_per_warp),
+            "tsplit": sc.tsplit}
+
+
 class Sampler:
     """Optimiser state of one tile (n_pairs independent 2-D problems) on the current device."""
 
@@ -81,12 +91,24 @@ class Sampler:
         L.check(L.load().bn_evaluate_energy(self._h, out))
         return np.array(out[:], np.float64)
 
+    def energy_into(self, device_ptr: int) -> None:
+        L.check(L.load().bn_evaluate_energy_device(self._h, device_ptr))
+
     def optimize(self, n_sweeps: int, stats: bool = True) -> SweepStats | None:
         st = L.BnSweepStats()
         L.check(L.load().bn_optimize_sweeps(self._h, n_sweeps, ctypes.byref(st) if stats else None))
         if not stats:
             return None
         return SweepStats(st.sweeps, st.proposals, st.improving, st.committed, st.ties)
+
+    def set_schedule(self, kind: int, shape=None, tsplit: int = 0) -> None:
+        sc = _schedule(kind, shape, tsplit)
+        L.check(L.load().bn_sampler_set_schedule(self._h, ctypes.byref(sc)))
+
+    def get_schedule(self) -> dict:
+        sc = L.BnSchedule()
+        L.check(L.load().bn_sampler_get_schedule(self._h, ctypes.byref(sc)))
+        return _unpack(sc)
 
     def reset(self, seed: int) -> None:
         L.check(L.load().bn_sampler_reset(self._h, seed))
@@ -169,6 +191,15 @@ class Batch:
         if not stats:
             return None
         return SweepStats(st.sweeps, st.proposals, st.improving, st.committed, st.ties)
+
+    def set_schedule(self, kind: int, shape=None, tsplit: int = 0) -> None:
+        sc = _schedule(kind, shape, tsplit)
+        L.check(L.load().bn_batch_set_schedule(self._h, ctypes.byref(sc)))
+
+    def get_schedule(self) -> dict:
+        sc = L.BnSchedule()
+        L.check(L.load().bn_batch_get_schedule(self._h, ctypes.byref(sc)))
+        return _unpack(sc)
 
     def close(self) -> None:
         if self._h:

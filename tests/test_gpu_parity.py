@@ -207,3 +207,73 @@ def test_full_size_gpu_scale_configuration(pkg):
     assert abs(s.energy()[0] - E) <= E_REL * E
     lockstep(s, [ref], 3)
     s.close()
+
+
+def test_lockstep_concurrent_mode(pkg):
+    s = pkg.Sampler(32, 32, 16, 64, seed=5, mode=pkg.BN_MODE_CONCURRENT)
+    ref = oracle.OracleTile(32, 32, 16, 64, seed=5, mode=oracle.MODE_CONCURRENT)
+    lockstep(s, [ref], 40)
+    s.close()
+
+
+@pytest.mark.parametrize("cfg", [(32, 32, 16, 64, 1, 6, 0), (45, 37, 4, 100, 1, 6, 3),
+                                 (16, 16, 256, 300, 2, 6, 5), (64, 32, 128, 130, 1, 6, 11)])
+def test_lockstep_persistent_schedule(pkg, cfg):
+    s = _sampler(pkg, cfg, schedule=pkg.BN_SCHEDULE_PERSISTENT)
+    assert s.get_schedule()["kind"] == pkg.BN_SCHEDULE_PERSISTENT
+    lockstep(s, _tiles(cfg), 30 if cfg[0] == 32 else 12, check_energy_every=10)
+    s.close()
+
+
+def test_persistent_lockstep_concurrent_mode(pkg):
+    s = pkg.Sampler(32, 32, 16, 64, seed=5, mode=pkg.BN_MODE_CONCURRENT,
+                    schedule=pkg.BN_SCHEDULE_PERSISTENT)
+    ref = oracle.OracleTile(32, 32, 16, 64, seed=5, mode=oracle.MODE_CONCURRENT)
+    lockstep(s, [ref], 30)
+    s.close()
+
+
+def _run_with(pkg, kind, shape, tsplit, cfg, sweeps):
+    W, H, N, T, pairs, seed = cfg
+    s = pkg.Sampler(W, H, N, T, seed=seed, n_pairs=pairs)
+    s.set_schedule(kind, shape, tsplit)
+    s.optimize(sweeps, stats=False)
+    out = (s.shifts(), s.sweep_log(0), s.energy())
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("cfg", [(64, 48, 64, 1024, 1, 21), (40, 40, 256, 200, 2, 4)])
+def test_schedule_does_not_change_results(pkg, cfg):
+    """Every instantiated CTA shape and chunk split of the persistent kernel, and the plain
+    schedule, produce bit-identical tiles, logs and energies."""
+    from paper_2105_12620_gb300._lib import PERSISTENT_SHAPES
+    base = _run_with(pkg, pkg.BN_SCHEDULE_PLAIN, None, 0, cfg, 25)
+    for shape in PERSISTENT_SHAPES:
+        for tsplit in (1, 2, 4):
+            got = _run_with(pkg, pkg.BN_SCHEDULE_PERSISTENT, shape, tsplit, cfg, 25)
+            assert np.array_equal(got[0], base[0]), (shape, tsplit)
+            for x, y in zip(got[1], base[1]):
+                assert np.array_equal(x, y), (shape, tsplit)
+            assert np.array_equal(got[2], base[2])
+
+
+def test_persistent_batch_equals_each_alone(pkg):
+    cfgs = [(32, 32, 16, 64, 1), (48, 40, 4, 256, 1), (64, 64, 64, 128, 2), (20, 36, 16, 1, 1),
+            (128, 128, 64, 1024, 1), (40, 24, 256, 128, 1)]
+    alone, mixed = [], []
+    for W, H, N, T, pairs in cfgs:
+        a = pkg.Sampler(W, H, N, T, seed=W + H, n_pairs=pairs, schedule=pkg.BN_SCHEDULE_PLAIN)
+        a.optimize(30, stats=False)
+        alone.append(a.shifts())
+        a.close()
+        mixed.append(pkg.Sampler(W, H, N, T, seed=W + H, n_pairs=pairs))
+    b = pkg.Batch(mixed)
+    assert b.get_schedule()["kind"] == pkg.BN_SCHEDULE_PERSISTENT
+    b.optimize(11, stats=False)
+    b.optimize(19, stats=False)
+    for m, ref in zip(mixed, alone):
+        assert np.array_equal(m.shifts(), ref)
+    b.close()
+    for m in mixed:
+        m.close()

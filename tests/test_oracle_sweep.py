@@ -109,3 +109,19 @@ def test_blue_objective_improves_blurred_error_and_literal_worsens_it():
     l0, l1 = res[oracle.OBJECTIVE_LITERAL]
     assert b1 < 0.8 * b0
     assert l1 > 1.2 * l0
+
+
+def test_concurrent_mode_keeps_every_improving_couple():
+    """Paper-literal commit (Sec. 3.4): all improving disjoint couples are applied together.
+    Every improving couple is kept; the loss change is then no longer the sum of the kept
+    changes, and early passes can move the loss the wrong way."""
+    t = oracle.OracleTile(32, 32, 16, 64, seed=1, mode=oracle.MODE_CONCURRENT)
+    logs, E = _run(t, 40)
+    nonadditive = 0
+    for s, lg in enumerate(logs):
+        imp = (lg.flags & FLAG_IMPROVING) != 0
+        assert np.array_equal(imp, (lg.flags & FLAG_COMMITTED) != 0)
+        if abs((E[s + 1] - E[s]) - lg.dE[imp].sum()) > 1e-9 * E[s]:
+            nonadditive += 1
+    assert nonadditive > 0
+    assert sorted(t.sidx.tolist()) == list(range(t.P))
