@@ -61,7 +61,7 @@ class BnSchedule(ctypes.Structure):
 
 
 # CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, slots/warp)
-PERSISTENT_SHAPES = [(16, 8, 512, 4), (8, 8, 256, 4), (16, 8, 1024, 2)]
+PERSISTENT_SHAPES = [(16, 8, 512, 4), (8, 16, 512, 4), (8, 8, 256, 4)]
 
 
 class BnError(RuntimeError):

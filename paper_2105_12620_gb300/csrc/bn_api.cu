@@ -94,12 +94,13 @@ namespace {
 // How the passes of a set of problems are executed, and the device arrays that go with it.
 struct SweepPlan {
     bool persistent = false;
-    bn::PersistentShape shape{16, 8, 512, 4, 1};
+    bn::PersistentShape shape{16, 8, 512, 4, 0};
     // per count width (index cb - 1): first problem, problem count, units / couples prefix
     int first[2] = {0, 0}, count[2] = {0, 0};
     int total_units[2] = {0, 0}, total_couples[2] = {0, 0};
     int *d_prefix = nullptr;        // [2][2][n_prob + 1] unit / couple prefix sums
     bn::GridBarrier *d_bar = nullptr;
+    int *d_work = nullptr;          // [2] phase-1 unit counters
     int n_prob = 0, max_M = 0, sms = 0;
 };
 
@@ -107,8 +108,10 @@ void free_plan(SweepPlan &pl)
 {
     if (pl.d_prefix) cudaFree(pl.d_prefix);
     if (pl.d_bar) cudaFree(pl.d_bar);
+    if (pl.d_work) cudaFree(pl.d_work);
     pl.d_prefix = nullptr;
     pl.d_bar = nullptr;
+    pl.d_work = nullptr;
 }
 
 }  // namespace
@@ -299,6 +302,31 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
         return fail(BN_ERR_INVALID_ARG,
                     "the persistent schedule needs radius 6 and tiles of at least 13 x 13");
     pl.persistent = ok && schedule != BN_SCHEDULE_PLAIN;
+    if (pl.persistent) {
+        // requested shape, else the first instantiated shape that fits every problem
+        std::vector<bn::PersistentShape> cands;
+        if (want) cands.push_back(*want);
+#define BN_CAND(BX, BY, NCW, SPW, MINB) cands.push_back(bn::PersistentShape{BX, BY, (NCW + 1) * 32, SPW, 0});
+        BN_PERSISTENT_SHAPES(BN_CAND)
+#undef BN_CAND
+        bool found = false;
+        for (auto &c : cands) {
+            bool fits = true;
+            for (auto &h : hp) fits = fits && bn::persistent_shape_fits(h, c);
+            if (fits) {
+                const int ts = want ? want->tsplit : 0;
+                pl.shape = c;
+                pl.shape.tsplit = ts;
+                found = true;
+                break;
+            }
+        }
+        if (!found) {
+            if (schedule == BN_SCHEDULE_PERSISTENT)
+                return fail(BN_ERR_INVALID_ARG, "no persistent CTA shape fits these tiles");
+            pl.persistent = false;
+        }
+    }
     for (int g = 0; g < 2; ++g) {
         pl.first[g] = pl.count[g] = 0;
         int f = -1;
@@ -313,7 +341,6 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
                 return fail(BN_ERR_INVALID_ARG, "internal: problems not grouped by count width");
     }
     if (!pl.persistent) return BN_OK;
-    if (want) pl.shape = *want;
     // default chunk split: enough work units to cover every SM twice
     int units1 = 0, min_chunks = 1 << 30;
     for (auto &h : hp) {
@@ -321,7 +348,7 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
         const int nc = h.row_bytes / 128;
         min_chunks = nc < min_chunks ? nc : min_chunks;
     }
-    if (!want || pl.shape.tsplit <= 0) {
+    if (pl.shape.tsplit <= 0) {
         int ts = (2 * pl.sms + units1 - 1) / units1;
         pl.shape.tsplit = ts;
     }
@@ -344,6 +371,7 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
     BN_CUDA(cudaMalloc(&pl.d_prefix, sizeof(int) * pre.size()));
     BN_CUDA(cudaMemcpy(pl.d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     BN_CUDA(cudaMalloc(&pl.d_bar, sizeof(bn::GridBarrier)));
+    BN_CUDA(cudaMalloc(&pl.d_work, 2 * sizeof(int)));
     (void)dprob;
     return BN_OK;
 }
@@ -373,9 +401,11 @@ int run_plan(const SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn
         a.total_couples = pl.total_couples[g];
         a.tsplit = pl.shape.tsplit;
         a.bar = pl.d_bar;
+        a.work = pl.d_work;
         for (int32_t done = 0; done < n_sweeps; done += kItersPerLaunch) {
             a.n_iter = n_sweeps - done < kItersPerLaunch ? n_sweeps - done : kItersPerLaunch;
             BN_CUDA(cudaMemsetAsync(pl.d_bar, 0, sizeof(bn::GridBarrier), st));
+            BN_CUDA(cudaMemsetAsync(pl.d_work, 0, 2 * sizeof(int), st));
             const bool timed = tm && tm->enabled;
             if (timed) tm->begin(bn::kKPersistent, st);
             cudaError_t e = bn::launch_persistent(a, pl.shape, g + 1, pl.sms, st);
@@ -748,8 +778,9 @@ static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Pro
     bn::PersistentShape shape{sc->block_x, sc->block_y, sc->threads, sc->slots_per_warp,
                               sc->tsplit};
     bool known = false;
-#define BN_KNOWN(BX, BY, NT, SPW, MINB)                                                       \
-    known = known || (shape.bx == BX && shape.by == BY && shape.threads == NT && shape.spw == SPW);
+#define BN_KNOWN(BX, BY, NCW, SPW, MINB)                                                      \
+    known = known || (shape.bx == BX && shape.by == BY && shape.threads == (NCW + 1) * 32 &&     \
+                      shape.spw == SPW);
     BN_PERSISTENT_SHAPES(BN_KNOWN)
 #undef BN_KNOWN
     const bool want_shape = sc->kind != BN_SCHEDULE_PLAIN && sc->block_x > 0;

@@ -1,7 +1,10 @@
 // bn_device.cuh — device-side data layout and helpers shared by the sampler's CUDA kernels.
 //
 // Layout of one problem (one 2-D pair of one tile) in device memory:
-//   counts   uint8/uint16 [P][row_bytes / count_bytes]  k_p[t], zero-padded to 128-B rows
+//   counts   chunk-major planes [row_bytes / 128][P][128 B]: bytes [128 c, 128 c + 128) of pixel
+//            p's count vector k_p (uint8 or uint16 per integrand, zero-padded to 128 B) live at
+//            counts + (c * P + p) * 128, so one chunk of a run of pixels of an image row is
+//            contiguous
 //   U        uint32 [P][2]    initial shifts u_p in 0.32 fixed point (low 8 bits zero)
 //   sidx     int32  [P]       index of the initial shift now at pixel p (a swap moves it)
 //   perm     int32  [2^L]     candidate permutation (Sec. 3.4), perm_inv its inverse
@@ -109,6 +112,19 @@ __device__ __forceinline__ int wrap_add(int v, int d, int n)
     v += (v < 0) ? n : 0;
     v -= (v >= n) ? n : 0;
     return v;
+}
+
+// chunk c of pixel p's count vector (128 bytes)
+__device__ __forceinline__ uint8_t *chunk_ptr(const Problem &pb, int p, int c)
+{
+    return pb.counts + (((size_t)c * pb.P + p) << 7);
+}
+
+// 16-byte piece vi (0 <= vi < row_bytes / 16) of pixel p's count vector
+__device__ __forceinline__ uint4 *vec_ptr(const Problem &pb, int p, int vi)
+{
+    return reinterpret_cast<uint4 *>(pb.counts + (((size_t)(vi >> 3) * pb.P + p) << 7) +
+                                     ((vi & 7) << 4));
 }
 
 // neighbour of pixel p at table offset i

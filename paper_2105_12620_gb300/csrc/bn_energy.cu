@@ -35,24 +35,21 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(const Problem *probs)
     if (p < pb.P) {
         const int nv = pb.row_bytes >> 4;
         const int px = p % pb.W, py = p / pb.W;
-        const uint4 *rp = reinterpret_cast<const uint4 *>(pb.counts + (size_t)p * pb.row_bytes);
         uint4 kp[kMaxVPL];
 #pragma unroll
         for (int v = 0; v < kMaxVPL; ++v) {
             const int vi = v * 32 + lane;
-            kp[v] = vi < nv ? rp[vi] : make_uint4(0u, 0u, 0u, 0u);
+            kp[v] = vi < nv ? *vec_ptr(pb, p, vi) : make_uint4(0u, 0u, 0u, 0u);
         }
         for (int c = 0; c < pb.n_cls; ++c) {
             int s = 0;
             for (int i = pb.cls_start[c]; i < pb.cls_start[c + 1]; ++i) {
                 const int q = neighbour(pb, px, py, i);
-                const uint4 *rq =
-                    reinterpret_cast<const uint4 *>(pb.counts + (size_t)q * pb.row_bytes);
 #pragma unroll
                 for (int v = 0; v < kMaxVPL; ++v) {
                     const int vi = v * 32 + lane;
                     if (vi < nv) {
-                        const uint4 k = rq[vi];
+                        const uint4 k = *vec_ptr(pb, q, vi);
                         s = sqdiff_word<CB>(kp[v].x, k.x, s);
                         s = sqdiff_word<CB>(kp[v].y, k.y, s);
                         s = sqdiff_word<CB>(kp[v].z, k.z, s);

@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(kCountThreads) k_counts(const Problem *probs)
                 cnt += (a * (long long)X + b * (long long)Y < C) ? 1 : 0;
             }
         }
-        reinterpret_cast<CT *>(pb.counts + (size_t)p * pb.row_bytes)[t] = (CT)cnt;
+        const int byte = t * (int)sizeof(CT);
+        reinterpret_cast<CT *>(chunk_ptr(pb, p, byte >> 7))[(byte & 127) / (int)sizeof(CT)] =
+            (CT)cnt;
     }
 }
 
@@ -146,7 +148,9 @@ __global__ void k_unpack_counts(const Problem *probs, int32_t *out)
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)pb.P * pb.T) return;
     const int p = (int)(i / pb.T), t = (int)(i % pb.T);
-    out[i] = reinterpret_cast<const CT *>(pb.counts + (size_t)p * pb.row_bytes)[t];
+    const int byte = t * (int)sizeof(CT);
+    out[i] = reinterpret_cast<const CT *>(chunk_ptr(pb, p, byte >> 7))[(byte & 127) /
+                                                                      (int)sizeof(CT)];
 }
 
 int perm_rounds(int L) { return 6 * L < 12 ? 12 : 6 * L; }

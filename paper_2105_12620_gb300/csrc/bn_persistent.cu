@@ -2,26 +2,27 @@
 // launch that runs many passes over a batch of problems (tiles x pairs of dimensions).
 //
 // Per pass, two phases separated by grid barriers:
-//   phase 1 (evaluate): the work unit is a block of BX x BY pixels of one problem and a range of
-//     128-byte chunks of the count vectors.  The CTA finds the block's proposed pixels (pixels
-//     that belong to a valid couple of this pass), stages the block's window (block plus a halo
-//     of the weight radius, wrapped on the torus) chunk by chunk into shared memory with
-//     cp.async double buffering, together with each proposed pixel's partner chunk, and every
-//     warp accumulates, for its proposed pixels, the exact integer sums
-//         A_c(p) += delta_p . k_q,   q in S_c(p),   delta_p = k_partner - k_p
+//   phase 1 (evaluate): CTAs take work units from an atomic counter.  A unit is a block of
+//     BX x BY pixels of one problem and a range of 128-byte chunks of the count vectors.  The
+//     CTA finds the block's proposed pixels (pixels of a valid couple of this pass).  One
+//     producer warp then streams, chunk by chunk, the block's window (the block plus a halo of
+//     the weight radius, wrapped on the torus) and each proposed pixel's partner chunk into a
+//     two-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion on
+//     an mbarrier); the counts are stored chunk-major, so every window row is one or two
+//     contiguous runs.  The compute warps accumulate, per proposed pixel p and class c,
+//         A_c(p) += delta_p . k_q  over q in S_c(p),   delta_p = k_partner - k_p,
 //     with the 112 stencil offsets as compile-time shared-memory displacements (one IDP4A per
-//     4 counts).  The contribution of the partner itself (when it lies in the neighbourhood) is
-//     removed afterwards.  Each side's class sums go to global memory; the last of the
-//     2 x tsplit contributions of a couple computes dL in fp32 (compensated), sets the flags,
-//     logs, and, if the swap improves the objective, claims the couple's two pixels in the
-//     owner grid of this pass's parity.
+//     four 8-bit counts).  The partner's own term is removed, the 18 class sums are reduced
+//     across the warp by a transposing butterfly and published; the last of the 2 x tsplit
+//     contributions of a couple computes dL in fp32 (compensated), flags and logs it and, if
+//     the swap improves the objective, claims the couple's pixels in the owner grid.
 //   phase 2 (resolve + commit): one warp per couple: an improving couple is kept unless an
 //     interacting improving couple (a pixel within the radius) has a higher priority; kept
-//     swaps move the count vectors and the shift index.  Owner entries of the previous pass are
+//     swaps move the count vectors and the shift index.  Owner claims of the previous pass are
 //     cleared here.
-// Data written inside the launch is read back with L2-only loads (.cg) because L1 is not
-// coherent across SMs.  Grid barriers spin with a clock budget; on timeout the kernel records
-// an error and every block returns.
+// Data written inside the launch is read back through L2 (.cg loads) because L1 is not coherent
+// across SMs.  Every wait (grid barrier, mbarrier) has a clock budget; when it runs out the
+// kernel records an error, lets its own copies land (again bounded) and returns.
 #include <utility>
 
 #include "bn_launch.h"
@@ -41,10 +42,8 @@ struct Stencil {
     int dx[(2 * R + 1) * (2 * R + 1)] = {};
     int dy[(2 * R + 1) * (2 * R + 1)] = {};
     int cls[(2 * R + 1) * (2 * R + 1)] = {};
-    int cls_of_d2[R * R + 1] = {};
     constexpr Stencil()
     {
-        for (int d = 0; d <= R * R; ++d) cls_of_d2[d] = -1;
         for (int d2 = 1; d2 <= R * R; ++d2) {
             bool any = false;
             for (int y = -R; y <= R; ++y)
@@ -56,10 +55,7 @@ struct Stencil {
                         ++n;
                         any = true;
                     }
-            if (any) {
-                cls_of_d2[d2] = ncls;
-                ++ncls;
-            }
+            if (any) ++ncls;
         }
     }
 };
@@ -68,7 +64,6 @@ constexpr int kNOff = kSt.n;
 constexpr int kNCls = kSt.ncls;
 static_assert(kNOff == 112 && kNCls == 18, "radius-6 stencil");
 
-// compile-time access to one offset (usable in device code)
 template <int I>
 struct StOff {
     static constexpr int dx = kSt.dx[I];
@@ -76,48 +71,58 @@ struct StOff {
     static constexpr int cls = kSt.cls[I];
 };
 
-// ---- memory helpers ---------------------------------------------------------------------
-__device__ __forceinline__ uint32_t ld_cg_u32(const void *p)
+// ---- PTX helpers -------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    uint32_t v;
-    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ int ld_cg_i32(const void *p) { return (int)ld_cg_u32(p); }
-__device__ __forceinline__ unsigned long long ld_cg_u64(const void *p)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    unsigned long long v;
-    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ uint4 ld_cg_v4(const void *p)
-{
-    uint4 v;
-    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-__device__ __forceinline__ void st_cg_v4(void *p, uint4 v)
-{
-    asm volatile("st.global.cg.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
-                 "r"(v.z), "r"(v.w)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+__device__ __forceinline__ void mbar_init_fence()
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ int warp_sum(int v)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false when the clock budget runs out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kBarrierSpinCycles) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 // ---- grid barrier (bounded spin) ----------------------------------------------------------
@@ -141,7 +146,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned int nblocks,
                     atomicExch(&gb->error, 1u);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -151,7 +156,6 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned int nblocks,
     return *s_err == 0;
 }
 
-// ---- problem lookup ------------------------------------------------------------------------
 __device__ __forceinline__ int find_problem(const int *start, int n, int u)
 {
     int lo = 0, hi = n - 1;
@@ -181,6 +185,23 @@ __device__ __forceinline__ void stencil_dot(const uint32_t *centre, uint32_t d, 
      ...);
 }
 
+// Butterfly that sums 32 per-lane vectors and transposes them: lane l returns the warp sum of
+// v[l].  16 + 8 + 4 + 2 + 1 = 31 shuffles.
+__device__ __forceinline__ int transpose_reduce32(int (&v)[32], int lane)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const int send = upper ? v[i] : v[i + off];
+            const int keep = upper ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, off);
+        }
+    }
+    return v[0];
+}
+
 struct Slot {
     int centre;   // window index of the pixel
     int j;        // couple
@@ -189,30 +210,39 @@ struct Slot {
     int cstar;    // class of the partner if it lies in the neighbourhood, else -1
 };
 
-template <int BX, int BY, int NT, int SPW, int CB>
+template <int BX, int BY, int NCW, int SPW>
 struct Cfg {
     static constexpr int WINW = BX + 2 * kR, WINH = BY + 2 * kR;
     static constexpr int WIN = WINW * WINH;
-    static constexpr int NWARPS = NT / 32;
-    static constexpr int CAP = NWARPS * SPW;  // slots per round
-    static constexpr int MAXSLOT = BX * BY;   // every pixel of the block
-    // one stage: window chunk + partner chunks of one round of slots
+    static constexpr int NT = (NCW + 1) * 32;      // compute warps + one producer warp
+    static constexpr int CAP = NCW * SPW;          // proposed pixels per round
+    static constexpr int MAXSLOT = BX * BY;
     static constexpr int STAGE = (WIN + CAP) * kChunk;
-    static constexpr size_t SMEM = 2 * (size_t)STAGE + MAXSLOT * sizeof(Slot) + 256;
+    static constexpr int OFF_SLOTS = 2 * STAGE;
+    static constexpr int OFF_BAR = (OFF_SLOTS + MAXSLOT * (int)sizeof(Slot) + 63) / 64 * 64;
+    static constexpr int OFF_MISC = OFF_BAR + 64;
+    static constexpr size_t SMEM = (size_t)OFF_MISC + 64;
 };
 
 // finish a couple once all its contributions have arrived: fp32 dL, flags, log, owner claim
 __device__ void finalize_couple(const Problem &pb, int j, uint32_t sw, int tsplit,
                                 unsigned int *bstat)
 {
-    int A[kNCls];
+    int A[20];
 #pragma unroll
-    for (int c = 0; c < kNCls; ++c) A[c] = 0;
+    for (int c = 0; c < 20; ++c) A[c] = 0;
     const int parts = 2 * tsplit;
     for (int k = 0; k < parts; ++k) {
-        const int *src = pb.side_cls + ((size_t)j * parts + k) * kMaxClasses;
+        const int4 *src =
+            reinterpret_cast<const int4 *>(pb.side_cls + ((size_t)j * parts + k) * kMaxClasses);
 #pragma unroll
-        for (int c = 0; c < kNCls; ++c) A[c] += ld_cg_i32(src + c);
+        for (int q = 0; q < 5; ++q) {
+            const int4 v = __ldcg(src + q);
+            A[4 * q] += v.x;
+            A[4 * q + 1] += v.y;
+            A[4 * q + 2] += v.z;
+            A[4 * q + 3] += v.w;
+        }
     }
     F2 acc = {0.f, 0.f};
     float sabs = 0.f;
@@ -244,11 +274,19 @@ __device__ void finalize_couple(const Problem &pb, int j, uint32_t sw, int tspli
     }
 }
 
-template <int BX, int BY, int NT, int SPW, int CB>
+// Shared state of the phase-1 pipeline of one CTA.
+struct Pipe {
+    uint64_t *full;   // [2] copies of a stage have landed
+    uint64_t *empty;  // [2] every compute warp is done with a stage
+    unsigned g;       // chunks streamed by this CTA so far (stage = g & 1)
+    unsigned issued;  // stage uses armed by the producer (for the abort path)
+};
+
+template <int BX, int BY, int NCW, int SPW, int CB>
 __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, int tsplit,
-                              char *smem, unsigned int *bstat)
+                              char *smem, unsigned int *bstat, Pipe &pp, volatile int *s_abort)
 {
-    using C = Cfg<BX, BY, NT, SPW, CB>;
+    using C = Cfg<BX, BY, NCW, SPW>;
     const int nbx = (pb.W + BX - 1) / BX;
     const int tpart = local_unit % tsplit;
     const int blk = local_unit / tsplit;
@@ -257,9 +295,8 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
     const int c0 = (int)((long long)nchunks * tpart / tsplit);
     const int c1 = (int)((long long)nchunks * (tpart + 1) / tsplit);
 
-    Slot *slots = reinterpret_cast<Slot *>(smem + 2 * C::STAGE);
-    int *s_nslot = reinterpret_cast<int *>(smem + 2 * C::STAGE + C::MAXSLOT * sizeof(Slot));
-    int *s_col = s_nslot + 1;            // tile x of each window column  [WINW]
+    Slot *slots = reinterpret_cast<Slot *>(smem + C::OFF_SLOTS);
+    int *s_nslot = reinterpret_cast<int *>(smem + C::OFF_MISC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // 1. proposed pixels of the block
@@ -267,7 +304,7 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
     __syncthreads();
     const uint32_t xs = pass_xor(pb, sw);
     const int twoM = 2 * pb.M;
-    for (int lp = threadIdx.x; lp < BX * BY; lp += NT) {
+    for (int lp = threadIdx.x; lp < BX * BY; lp += C::NT) {
         const int x = x0 + lp % BX, y = y0 + lp / BX;
         if (x >= pb.W || y >= pb.H) continue;
         const int p = y * pb.W + x;
@@ -288,95 +325,116 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
             if (pb.d2[c] == d2) s.cstar = c;
         slots[atomicAdd(s_nslot, 1)] = s;
     }
-    for (int wx = threadIdx.x; wx < C::WINW; wx += NT) s_col[wx] = wrapi(x0 - kR + wx, pb.W);
     __syncthreads();
     const int nslot = *s_nslot;
     if (nslot == 0) return;
-
-    uint32_t *stage[2] = {reinterpret_cast<uint32_t *>(smem),
-                          reinterpret_cast<uint32_t *>(smem + C::STAGE)};
     const int parts = 2 * tsplit;
+    const int xa = x0 - kR, xb = x0 + BX + kR;  // window columns [xa, xb), W >= xb - xa
 
     for (int base = 0; base < nslot; base += C::CAP) {
         const int nround = min(C::CAP, nslot - base);
-        int acc[SPW][kNCls];
-        int corr[SPW];
-#pragma unroll
-        for (int k = 0; k < SPW; ++k) {
-            corr[k] = 0;
-#pragma unroll
-            for (int c = 0; c < kNCls; ++c) acc[k][c] = 0;
-        }
-        auto issue = [&](int chunk, uint32_t *dst) {
-            const size_t coff = (size_t)chunk * kChunk;
-            for (int e = threadIdx.x; e < C::WIN * (kChunk / 16); e += NT) {
-                const int wp = e / (kChunk / 16), part = e % (kChunk / 16);
-                const int wx = wp % C::WINW, wy = wp / C::WINW;
-                const int ty = wrapi(y0 - kR + wy, pb.H);
-                const int q = ty * pb.W + s_col[wx];
-                cp_async16(reinterpret_cast<char *>(dst) + (size_t)wp * kChunk + part * 16,
-                           pb.counts + (size_t)q * pb.row_bytes + coff + part * 16);
+        const int nch = c1 - c0;
+        if (warp == NCW) {
+            // ---------------- producer warp ----------------
+            const uint32_t tx = (uint32_t)(C::WIN + nround) * kChunk;
+            for (int k = 0; k < nch; ++k) {
+                const unsigned g = pp.g + k, st = g & 1u, use = g >> 1;
+                const bool ok = use < 1 || mbar_wait(&pp.empty[st], (use - 1) & 1u);
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    if (lane == 0) *s_abort = 1;
+                    break;
+                }
+                if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? *s_abort : 0, 0)) break;
+                char *dst = smem + st * C::STAGE;
+                const int c = c0 + k;
+                if (lane == 0) mbar_arrive_expect_tx(&pp.full[st], tx);
+                __syncwarp();
+                for (int wy = lane; wy < C::WINH; wy += 32) {
+                    const int ty = wrapi(y0 - kR + wy, pb.H);
+                    const uint8_t *rowp = chunk_ptr(pb, ty * pb.W, c);
+                    char *d = dst + (size_t)wy * C::WINW * kChunk;
+                    if (xa < 0) {
+                        bulk_g2s(d, rowp + (size_t)(pb.W + xa) * kChunk, (uint32_t)(-xa) * kChunk,
+                                 &pp.full[st]);
+                        bulk_g2s(d + (size_t)(-xa) * kChunk, rowp, (uint32_t)xb * kChunk,
+                                 &pp.full[st]);
+                    } else if (xb > pb.W) {
+                        bulk_g2s(d, rowp + (size_t)xa * kChunk, (uint32_t)(pb.W - xa) * kChunk,
+                                 &pp.full[st]);
+                        bulk_g2s(d + (size_t)(pb.W - xa) * kChunk, rowp,
+                                 (uint32_t)(xb - pb.W) * kChunk, &pp.full[st]);
+                    } else {
+                        bulk_g2s(d, rowp + (size_t)xa * kChunk, (uint32_t)(xb - xa) * kChunk,
+                                 &pp.full[st]);
+                    }
+                }
+                for (int sl = lane; sl < nround; sl += 32)
+                    bulk_g2s(dst + (size_t)(C::WIN + sl) * kChunk,
+                             chunk_ptr(pb, slots[base + sl].partner, c), kChunk, &pp.full[st]);
+                pp.issued = g + 1;
             }
-            for (int e = threadIdx.x; e < nround * (kChunk / 16); e += NT) {
-                const int sl = e / (kChunk / 16), part = e % (kChunk / 16);
-                const int q = slots[base + sl].partner;
-                cp_async16(reinterpret_cast<char *>(dst) + (size_t)(C::WIN + sl) * kChunk + part * 16,
-                           pb.counts + (size_t)q * pb.row_bytes + coff + part * 16);
-            }
-            cp_async_commit();
-        };
-        issue(c0, stage[0]);
-        for (int c = c0; c < c1; ++c) {
-            const int cur = (c - c0) & 1;
-            if (c + 1 < c1) {
-                issue(c + 1, stage[cur ^ 1]);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            const uint32_t *win = stage[cur];
+        } else {
+            // ---------------- compute warps ----------------
+            int acc[SPW][kNCls];
+            int corr[SPW];
 #pragma unroll
             for (int k = 0; k < SPW; ++k) {
-                const int sl = warp + k * C::NWARPS;
-                if (sl < nround) {
-                    const Slot s = slots[base + sl];
-                    const uint32_t *centre = win + (size_t)s.centre * kChunkWords + lane;
-                    const uint32_t kp = *centre;
-                    const uint32_t kq = win[(size_t)(C::WIN + sl) * kChunkWords + lane];
-                    const uint32_t d = sub_word<CB>(kq, kp);
-                    corr[k] = dot_word<CB>(d, kq, corr[k]);
-                    stencil_dot<CB, C::WINW>(centre, d, acc[k],
-                                             std::make_integer_sequence<int, kNOff>{});
+                corr[k] = 0;
+#pragma unroll
+                for (int c = 0; c < kNCls; ++c) acc[k][c] = 0;
+            }
+            for (int k = 0; k < nch; ++k) {
+                const unsigned g = pp.g + k, st = g & 1u, use = g >> 1;
+                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&pp.full[st], use & 1u))) {
+                    if (lane == 0) *s_abort = 1;
+                    break;
                 }
-            }
-            __syncthreads();
-        }
-        // 3. per slot: reduce, remove the partner's own term, publish, finalize if last
+                const uint32_t *win = reinterpret_cast<const uint32_t *>(smem + st * C::STAGE);
 #pragma unroll
-        for (int k = 0; k < SPW; ++k) {
-            const int sl = warp + k * C::NWARPS;
-            if (sl >= nround) continue;
-            const Slot s = slots[base + sl];
-            const int cr = warp_sum(corr[k]);
-            int *dst = pb.side_cls + ((size_t)s.j * parts + s.side * tsplit + tpart) * kMaxClasses;
-#pragma unroll
-            for (int c = 0; c < kNCls; ++c) {
-                int v = warp_sum(acc[k][c]);
-                if (c == s.cstar) v -= cr;
-                if (lane == 0) dst[c] = v;
+                for (int q = 0; q < SPW; ++q) {
+                    const int sl = warp + q * NCW;
+                    if (sl < nround) {
+                        const int centre_idx = slots[base + sl].centre;
+                        const uint32_t *centre = win + (size_t)centre_idx * kChunkWords + lane;
+                        const uint32_t kp = *centre;
+                        const uint32_t kq = win[(size_t)(C::WIN + sl) * kChunkWords + lane];
+                        const uint32_t d = sub_word<CB>(kq, kp);
+                        corr[q] = dot_word<CB>(d, kq, corr[q]);
+                        stencil_dot<CB, C::WINW>(centre, d, acc[q],
+                                                 std::make_integer_sequence<int, kNOff>{});
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&pp.empty[st]);
             }
-            if (lane == 0) {
+            // publish: per slot, the 18 class sums of this side and chunk range
+#pragma unroll
+            for (int q = 0; q < SPW; ++q) {
+                const int sl = warp + q * NCW;
+                if (sl >= nround) continue;
+                const Slot s = slots[base + sl];
+                int v[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    v[c] = c < kNCls ? acc[q][c] - (c == s.cstar ? corr[q] : 0) : 0;
+                const int sum = transpose_reduce32(v, lane);
+                int *dst = pb.side_cls + ((size_t)s.j * parts + s.side * tsplit + tpart) * kMaxClasses;
+                if (lane < kNCls) dst[lane] = sum;
                 __threadfence();
-                const int arrived = atomicAdd(pb.arrivals + s.j, 1);
-                if (arrived == parts - 1) {
-                    __threadfence();
-                    pb.arrivals[s.j] = 0;
-                    finalize_couple(pb, s.j, sw, tsplit, bstat);
+                __syncwarp();
+                if (lane == 0) {
+                    const int arrived = atomicAdd(pb.arrivals + s.j, 1);
+                    if (arrived == parts - 1) {
+                        __threadfence();
+                        pb.arrivals[s.j] = 0;
+                        finalize_couple(pb, s.j, sw, tsplit, bstat);
+                    }
                 }
             }
         }
+        pp.g += nch;
         __syncthreads();
+        if (*s_abort) return;
     }
 }
 
@@ -405,9 +463,9 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
         }
         return false;
     }
-    const uint8_t flags = (uint8_t)(ld_cg_u32(reinterpret_cast<const uint32_t *>(
-                                        pb.log_flags + (j & ~3))) >>
-                                    (8 * (j & 3)));
+    const uint8_t flags =
+        (uint8_t)(__ldcg(reinterpret_cast<const unsigned int *>(pb.log_flags + (j & ~3))) >>
+                  (8 * (j & 3)));
     if (!(flags & kFlagImproving)) return false;
     bool win = true;
     if (pb.mode == 0) {
@@ -418,54 +476,85 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
             const int side = i >= pb.n_off;
             const int p = side ? b : a;
             const int q = neighbour(pb, p % pb.W, p / pb.W, side ? i - pb.n_off : i);
-            if (ld_cg_u64(own + q) > key) lose = true;
+            if (__ldcg(own + q) > key) lose = true;
         }
         win = !__any_sync(0xFFFFFFFFu, lose);
     }
     if (!win) return false;
-    uint8_t *ra = pb.counts + (size_t)a * pb.row_bytes;
-    uint8_t *rb = pb.counts + (size_t)b * pb.row_bytes;
-    for (int v = lane; v < (pb.row_bytes >> 4); v += 32) {
-        const uint4 x = ld_cg_v4(ra + 16 * v), y = ld_cg_v4(rb + 16 * v);
-        st_cg_v4(ra + 16 * v, y);
-        st_cg_v4(rb + 16 * v, x);
+    for (int vi = lane; vi < (pb.row_bytes >> 4); vi += 32) {
+        uint4 *pa = vec_ptr(pb, a, vi), *pbp = vec_ptr(pb, b, vi);
+        const uint4 x = __ldcg(pa), y = __ldcg(pbp);
+        __stcg(pa, y);
+        __stcg(pbp, x);
     }
     if (lane == 0) {
-        const int t = ld_cg_i32(pb.sidx + a);
-        pb.sidx[a] = ld_cg_i32(pb.sidx + b);
+        const int t = __ldcg(pb.sidx + a);
+        pb.sidx[a] = __ldcg(pb.sidx + b);
         pb.sidx[b] = t;
         pb.log_flags[j] = flags | kFlagCommitted;
     }
     return lane == 0;
 }
 
-template <int BX, int BY, int NT, int SPW, int CB, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_persistent(PersistentArgs args)
+template <int BX, int BY, int NCW, int SPW, int CB, int MINB>
+__global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentArgs args)
 {
+    using C = Cfg<BX, BY, NCW, SPW>;
     extern __shared__ __align__(128) char smem[];
-    __shared__ int s_err;
+    __shared__ int s_err, s_unit;
+    __shared__ int s_abort;
     __shared__ unsigned int bstat[4];
     const int nblocks = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * (NT / 32) + warp, nwarps = nblocks * (NT / 32);
+    const int gwarp = blockIdx.x * (C::NT / 32) + warp, nwarps = nblocks * (C::NT / 32);
+
+    Pipe pp;
+    pp.full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    pp.empty = pp.full + 2;
+    pp.g = 0;
+    pp.issued = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&pp.full[0], 1);
+        mbar_init(&pp.full[1], 1);
+        mbar_init(&pp.empty[0], NCW);
+        mbar_init(&pp.empty[1], NCW);
+        mbar_init_fence();
+        s_abort = 0;
+        s_err = 0;
+    }
+    __syncthreads();
 
     for (int it = 0; it < args.n_iter; ++it) {
-        // ---- phase 1: evaluate -------------------------------------------------------------
-        for (int u = blockIdx.x; u < args.total_units; u += nblocks) {
+        // ---- phase 1: evaluate (units from an atomic counter) -------------------------------
+        for (;;) {
+            if (threadIdx.x == 0) s_unit = atomicAdd(args.work + (it & 1), 1);
+            __syncthreads();
+            const int u = s_unit;
+            if (u >= args.total_units) break;
             const int pi = find_problem(args.unit_start, args.n_prob, u);
             const Problem &pb = args.probs[pi];
             const long long s = pb.ctr[0] + it;
-            if (s >= pb.ctr[1]) continue;
-            if (threadIdx.x < 4) bstat[threadIdx.x] = 0u;
+            if (s < pb.ctr[1]) {
+                if (threadIdx.x < 4) bstat[threadIdx.x] = 0u;
+                __syncthreads();
+                evaluate_unit<BX, BY, NCW, SPW, CB>(pb, u - __ldg(args.unit_start + pi),
+                                                    (uint32_t)s, args.tsplit, smem, bstat, pp,
+                                                    &s_abort);
+                __syncthreads();
+                if (threadIdx.x < 4 && bstat[threadIdx.x])
+                    atomicAdd(&pb.stats[threadIdx.x], (unsigned long long)bstat[threadIdx.x]);
+            }
+            const int ab = s_abort;
             __syncthreads();
-            evaluate_unit<BX, BY, NT, SPW, CB>(pb, u - __ldg(args.unit_start + pi), (uint32_t)s,
-                                               args.tsplit, smem, bstat);
-            __syncthreads();
-            if (threadIdx.x < 4 && bstat[threadIdx.x])
-                atomicAdd(&pb.stats[threadIdx.x], (unsigned long long)bstat[threadIdx.x]);
+            if (ab) break;
         }
-        if (!grid_sync(args.bar, nblocks, &s_err)) return;
+        if (s_abort) {
+            if (threadIdx.x == 0) atomicExch(&args.bar->error, 2u);
+            break;
+        }
+        if (!grid_sync(args.bar, nblocks, &s_err)) break;
         // ---- phase 2: resolve + commit -------------------------------------------------------
+        if (blockIdx.x == 0 && threadIdx.x == 0) args.work[(it + 1) & 1] = 0;
         int cur_pi = -1;
         unsigned int mine = 0u;
         for (int g = gwarp; g < args.total_couples; g += nwarps) {
@@ -483,7 +572,15 @@ __global__ void __launch_bounds__(NT, MINB) k_persistent(PersistentArgs args)
         }
         if (cur_pi >= 0 && mine && lane == 0)
             atomicAdd(&args.probs[cur_pi].stats[kStatCommitted], (unsigned long long)mine);
-        if (!grid_sync(args.bar, nblocks, &s_err)) return;
+        if (!grid_sync(args.bar, nblocks, &s_err)) break;
+    }
+    if (s_abort || s_err) {
+        // let this CTA's own copies land before it leaves (bounded)
+        if (warp == NCW && lane == 0)
+            for (unsigned g = (pp.issued >= 2 ? pp.issued - 2 : 0); g < pp.issued; ++g)
+                mbar_wait(&pp.full[g & 1u], (g >> 1) & 1u);
+        __syncthreads();
+        return;
     }
     // ---- epilogue: clear the last pass's owner claims, advance the pass counters ------------
     for (int g = gwarp; g < args.total_couples; g += nwarps) {
@@ -502,7 +599,7 @@ __global__ void __launch_bounds__(NT, MINB) k_persistent(PersistentArgs args)
     }
     if (!grid_sync(args.bar, nblocks, &s_err)) return;
     if (blockIdx.x == 0) {
-        for (int pi = threadIdx.x; pi < args.n_prob; pi += NT) {
+        for (int pi = threadIdx.x; pi < args.n_prob; pi += C::NT) {
             const Problem &pb = args.probs[pi];
             const long long s0 = pb.ctr[0];
             const long long done = max(0ll, min(s0 + args.n_iter, pb.ctr[1]) - s0);
@@ -512,28 +609,27 @@ __global__ void __launch_bounds__(NT, MINB) k_persistent(PersistentArgs args)
     }
 }
 
-template <int BX, int BY, int NT, int SPW, int CB, int MINB>
-cudaError_t launch_cfg(const PersistentArgs &a0, int sms, cudaStream_t st, int *grid_out)
+template <int BX, int BY, int NCW, int SPW, int CB, int MINB>
+cudaError_t launch_cfg(const PersistentArgs &a0, int sms, cudaStream_t st)
 {
-    using C = Cfg<BX, BY, NT, SPW, CB>;
-    auto kern = k_persistent<BX, BY, NT, SPW, CB, MINB>;
+    using C = Cfg<BX, BY, NCW, SPW>;
+    auto kern = k_persistent<BX, BY, NCW, SPW, CB, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, C::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, C::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = per_sm * sms;
-    const int need = a0.total_units > a0.total_couples / (NT / 32)
+    const int need = a0.total_units > a0.total_couples / (C::NT / 32)
                          ? a0.total_units
-                         : (a0.total_couples + NT / 32 - 1) / (NT / 32);
+                         : (a0.total_couples + C::NT / 32 - 1) / (C::NT / 32);
     if (grid > need) grid = need > 0 ? need : 1;
     PersistentArgs a = a0;
     void *params[] = {&a};
-    *grid_out = grid;
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(NT), params, C::SMEM,
-                                       st);
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(C::NT), params,
+                                       C::SMEM, st);
 }
 
 }  // namespace
@@ -549,15 +645,20 @@ bool persistent_supported(const Problem &h)
            h.n_off == kNOff;
 }
 
+bool persistent_shape_fits(const Problem &h, const PersistentShape &s)
+{
+    // a window row must wrap at most once
+    return persistent_supported(h) && h.W >= s.bx + 2 * kR;
+}
+
 cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &shape, int cb,
                               int sms, cudaStream_t st)
 {
-    int grid = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define BN_SHAPE(BX, BY, NT, SPW, MINB)                                                      \
-    if (shape.bx == BX && shape.by == BY && shape.threads == NT && shape.spw == SPW)         \
-        e = cb == 1 ? launch_cfg<BX, BY, NT, SPW, 1, MINB>(a, sms, st, &grid)                \
-                    : launch_cfg<BX, BY, NT, SPW, 2, MINB>(a, sms, st, &grid);
+#define BN_SHAPE(BX, BY, NCW, SPW, MINB)                                                      \
+    if (shape.bx == BX && shape.by == BY && shape.threads == (NCW + 1) * 32 && shape.spw == SPW) \
+        e = cb == 1 ? launch_cfg<BX, BY, NCW, SPW, 1, MINB>(a, sms, st)                      \
+                    : launch_cfg<BX, BY, NCW, SPW, 2, MINB>(a, sms, st);
     BN_PERSISTENT_SHAPES(BN_SHAPE)
 #undef BN_SHAPE
     note_launches(1);

@@ -27,6 +27,7 @@ struct PersistentArgs {
     int tsplit;
     int n_iter;             // passes in this launch (problems stop at their own pass end)
     GridBarrier *bar;
+    int *work;              // [2] unit counters of phase 1, by pass parity; zeroed per launch
 };
 
 // CTA shape: block of bx x by pixels, threads per CTA, proposed pixels per warp per round
@@ -34,14 +35,16 @@ struct PersistentShape {
     int bx, by, threads, spw, tsplit;
 };
 
-// Instantiated CTA shapes: X(bx, by, threads, slots per warp, min CTAs per SM)
+// Instantiated CTA shapes: X(bx, by, compute warps, slots per warp per round, min CTAs per SM);
+// every CTA has one more warp, the producer (threads = 32 * (compute warps + 1)).
 #define BN_PERSISTENT_SHAPES(X) \
-    X(16, 8, 512, 4, 1)         \
-    X(8, 8, 256, 4, 2)          \
-    X(16, 8, 1024, 2, 1)
+    X(16, 8, 15, 4, 1)          \
+    X(8, 16, 15, 4, 1)          \
+    X(8, 8, 7, 4, 2)
 
 int persistent_units_per_problem(const Problem &h, int bx, int by, int tsplit);
 bool persistent_supported(const Problem &h);
+bool persistent_shape_fits(const Problem &h, const PersistentShape &s);
 cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &shape, int cb,
                               int sms, cudaStream_t st);
 

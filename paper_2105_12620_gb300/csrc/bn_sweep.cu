@@ -27,11 +27,6 @@ __device__ __forceinline__ int warp_sum(int v)
     return v;
 }
 
-__device__ __forceinline__ const uint4 *row(const Problem &pb, int p)
-{
-    return reinterpret_cast<const uint4 *>(pb.counts + (size_t)p * pb.row_bytes);
-}
-
 // fp32 change of Eq. 1 from the exact class sums; also the sum of absolute terms
 __device__ __forceinline__ void couple_delta(const Problem &pb, const int *A, float &dL,
                                              float &S)
@@ -71,12 +66,12 @@ __global__ void __launch_bounds__(kPlainThreads) k_eval_plain(const Problem *pro
         uint8_t flags = 0;
         if (a < pb.P && b < pb.P) {
             const int nv = pb.row_bytes >> 4;
-            const uint4 *ra = row(pb, a), *rb = row(pb, b);
             uint4 d[kMaxVPL];
 #pragma unroll
             for (int v = 0; v < kMaxVPL; ++v) {
                 const int vi = v * 32 + lane;
-                d[v] = vi < nv ? sub_vec<CB>(rb[vi], ra[vi]) : make_uint4(0u, 0u, 0u, 0u);
+                d[v] = vi < nv ? sub_vec<CB>(*vec_ptr(pb, b, vi), *vec_ptr(pb, a, vi))
+                               : make_uint4(0u, 0u, 0u, 0u);
             }
             int A[kMaxClasses];
 #pragma unroll
@@ -91,11 +86,10 @@ __global__ void __launch_bounds__(kPlainThreads) k_eval_plain(const Problem *pro
                         for (int i = pb.cls_start[c]; i < pb.cls_start[c + 1]; ++i) {
                             const int q = neighbour(pb, px, py, i);
                             if (q == partner) continue;
-                            const uint4 *rq = row(pb, q);
 #pragma unroll
                             for (int v = 0; v < kMaxVPL; ++v) {
                                 const int vi = v * 32 + lane;
-                                if (vi < nv) part = dot_vec<CB>(d[v], rq[vi], part);
+                                if (vi < nv) part = dot_vec<CB>(d[v], *vec_ptr(pb, q, vi), part);
                             }
                         }
                         acc += side ? -part : part;
@@ -186,12 +180,11 @@ __global__ void __launch_bounds__(kPlainThreads) k_commit_plain(const Problem *p
             own[b] = 0ull;
         }
         if (flags & kFlagCommitted) {
-            uint4 *ra = reinterpret_cast<uint4 *>(pb.counts + (size_t)a * pb.row_bytes);
-            uint4 *rb = reinterpret_cast<uint4 *>(pb.counts + (size_t)b * pb.row_bytes);
             for (int vi = lane; vi < (pb.row_bytes >> 4); vi += 32) {
-                const uint4 t = ra[vi];
-                ra[vi] = rb[vi];
-                rb[vi] = t;
+                uint4 *ra = vec_ptr(pb, a, vi), *rb = vec_ptr(pb, b, vi);
+                const uint4 t = *ra;
+                *ra = *rb;
+                *rb = t;
             }
             if (lane == 0) {
                 const int t = pb.sidx[a];

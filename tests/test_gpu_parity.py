@@ -217,11 +217,12 @@ def test_lockstep_concurrent_mode(pkg):
 
 
 @pytest.mark.parametrize("cfg", [(32, 32, 16, 64, 1, 6, 0), (45, 37, 4, 100, 1, 6, 3),
-                                 (16, 16, 256, 300, 2, 6, 5), (64, 32, 128, 130, 1, 6, 11)])
+                                 (24, 20, 256, 300, 2, 6, 5), (64, 32, 128, 130, 1, 6, 11),
+                                 (20, 13, 16, 40, 1, 6, 12)])
 def test_lockstep_persistent_schedule(pkg, cfg):
     s = _sampler(pkg, cfg, schedule=pkg.BN_SCHEDULE_PERSISTENT)
     assert s.get_schedule()["kind"] == pkg.BN_SCHEDULE_PERSISTENT
-    lockstep(s, _tiles(cfg), 30 if cfg[0] == 32 else 12, check_energy_every=10)
+    lockstep(s, _tiles(cfg), 30 if cfg[0] == 32 else 12, check_energy_every=6)
     s.close()
 
 
