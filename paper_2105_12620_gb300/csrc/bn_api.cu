@@ -261,7 +261,6 @@ void carve(Slab &s, bn::Problem &h)
     h.log_flags = s.take<uint8_t>((size_t)h.M + 4);  // phase 2 reads aligned 4-byte words
     h.log_couples = s.take<int32_t>((size_t)h.M * 2);
     h.side_cls = s.take<int32_t>((size_t)h.M * 2 * bn::kMaxTsplit * bn::kMaxClasses);
-    h.arrivals = s.take<int32_t>(h.M);
     h.ctr = s.take<long long>(4);
     h.stats = s.take<unsigned long long>(bn::kStatCount);
     h.esum = s.take<unsigned long long>(bn::kMaxClasses);

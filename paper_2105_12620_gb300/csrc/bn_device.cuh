@@ -57,8 +57,7 @@ struct Problem {
     float *log_dE;
     uint8_t *log_flags;
     int32_t *log_couples;
-    int32_t *side_cls;         // [M][2][kMaxClasses] per-side class sums (blocked evaluator)
-    int32_t *arrivals;         // [M] sides finished (blocked evaluator)
+    int32_t *side_cls;         // [M][2 x tsplit][kMaxClasses] partial class sums (persistent)
     long long *ctr;            // [0] pass counter, [1] pass end, [2] ticket
     unsigned long long *stats; // [kStatCount]
     unsigned long long *esum;  // [kMaxClasses] energy class sums (two's complement int64)

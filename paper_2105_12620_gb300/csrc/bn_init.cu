@@ -71,7 +71,6 @@ __global__ void k_clear_state(const Problem *probs)
     const Problem &pb = *probs;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 2 * pb.P) pb.owner[i] = 0ull;
-    if (i < pb.M) pb.arrivals[i] = 0;
     if (i < kStatCount) pb.stats[i] = 0ull;
     if (i < 4) pb.ctr[i] = 0;
 }

@@ -1,7 +1,7 @@
 // bn_persistent.cu — the parallel swap optimiser (Sec. 3.4) as one cooperative, persistent
 // launch that runs many passes over a batch of problems (tiles x pairs of dimensions).
 //
-// Per pass, two phases separated by grid barriers:
+// Per pass, three phases separated by grid barriers:
 //   phase 1 (evaluate): CTAs take work units from an atomic counter.  A unit is a block of
 //     BX x BY pixels of one problem and a range of 128-byte chunks of the count vectors.  The
 //     CTA finds the block's proposed pixels (pixels of a valid couple of this pass).  One
@@ -9,14 +9,16 @@
 //     the weight radius, wrapped on the torus) and each proposed pixel's partner chunk into a
 //     two-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion on
 //     an mbarrier); the counts are stored chunk-major, so every window row is one or two
-//     contiguous runs.  The compute warps accumulate, per proposed pixel p and class c,
+//     contiguous runs.  The compute warps read their proposed pixels' partner chunks straight
+//     from L2 (prefetched one chunk ahead) and accumulate, per proposed pixel p and class c,
 //         A_c(p) += delta_p . k_q  over q in S_c(p),   delta_p = k_partner - k_p,
 //     with the 112 stencil offsets as compile-time shared-memory displacements (one IDP4A per
-//     four 8-bit counts).  The partner's own term is removed, the 18 class sums are reduced
-//     across the warp by a transposing butterfly and published; the last of the 2 x tsplit
-//     contributions of a couple computes dL in fp32 (compensated), flags and logs it and, if
-//     the swap improves the objective, claims the couple's pixels in the owner grid.
-//   phase 2 (resolve + commit): one warp per couple: an improving couple is kept unless an
+//     four 8-bit counts).  The partner's own term is removed and the 18 class sums are reduced
+//     across the warp by a transposing butterfly and stored.
+//   phase 2 (finalize): one thread per couple adds the 2 x tsplit partial class sums, computes
+//     dL in fp32 (compensated), flags and logs it and, if the swap improves the objective,
+//     claims the couple's pixels in the owner grid.
+//   phase 3 (resolve + commit): one warp per couple: an improving couple is kept unless an
 //     interacting improving couple (a pixel within the radius) has a higher priority; kept
 //     swaps move the count vectors and the shift index.  Owner claims of the previous pass are
 //     cleared here.
@@ -217,17 +219,26 @@ struct Cfg {
     static constexpr int NT = (NCW + 1) * 32;      // compute warps + one producer warp
     static constexpr int CAP = NCW * SPW;          // proposed pixels per round
     static constexpr int MAXSLOT = BX * BY;
-    static constexpr int STAGE = (WIN + CAP) * kChunk;
+    static constexpr int STAGE = WIN * kChunk;
     static constexpr int OFF_SLOTS = 2 * STAGE;
     static constexpr int OFF_BAR = (OFF_SLOTS + MAXSLOT * (int)sizeof(Slot) + 63) / 64 * 64;
     static constexpr int OFF_MISC = OFF_BAR + 64;
     static constexpr size_t SMEM = (size_t)OFF_MISC + 64;
 };
 
-// finish a couple once all its contributions have arrived: fp32 dL, flags, log, owner claim
-__device__ void finalize_couple(const Problem &pb, int j, uint32_t sw, int tsplit,
-                                unsigned int *bstat)
+// finish a couple after phase 1: fp32 dL, flags, log, owner claim (one thread); returns flags
+__device__ uint8_t finalize_couple(const Problem &pb, int j, uint32_t sw, int tsplit)
 {
+    const uint32_t xs = pass_xor(pb, sw);
+    const int a = (int)((uint32_t)__ldg(pb.perm + 2 * j) ^ xs);
+    const int b = (int)((uint32_t)__ldg(pb.perm + 2 * j + 1) ^ xs);
+    pb.log_couples[2 * j] = a;
+    pb.log_couples[2 * j + 1] = b;
+    if (a >= pb.P || b >= pb.P) {
+        pb.log_dE[j] = 0.f;
+        pb.log_flags[j] = 0;
+        return 0;
+    }
     int A[20];
 #pragma unroll
     for (int c = 0; c < 20; ++c) A[c] = 0;
@@ -256,22 +267,16 @@ __device__ void finalize_couple(const Problem &pb, int j, uint32_t sw, int tspli
     const float S = pb.scale * sabs;
     const bool improving = (float)pb.objective * dL < 0.f;
     const bool tie = fabsf(dL) < 1e-6f * S;
-    const uint32_t xs = pass_xor(pb, sw);
-    const int a = (int)((uint32_t)__ldg(pb.perm + 2 * j) ^ xs);
-    const int b = (int)((uint32_t)__ldg(pb.perm + 2 * j + 1) ^ xs);
+    const uint8_t flags = kFlagValid | (improving ? kFlagImproving : 0) | (tie ? kFlagTie : 0);
     pb.log_dE[j] = dL;
-    pb.log_flags[j] = kFlagValid | (improving ? kFlagImproving : 0) | (tie ? kFlagTie : 0);
-    pb.log_couples[2 * j] = a;
-    pb.log_couples[2 * j + 1] = b;
-    atomicAdd(&bstat[kStatValid], 1u);
-    if (improving) atomicAdd(&bstat[kStatImproving], 1u);
-    if (tie) atomicAdd(&bstat[kStatTies], 1u);
+    pb.log_flags[j] = flags;
     if (improving && pb.mode == 0) {
         const unsigned long long key = couple_key(pb, sw, j);
         unsigned long long *own = pb.owner + (size_t)(sw & 1u) * pb.P;
         own[a] = key;
         own[b] = key;
     }
+    return flags;
 }
 
 // Shared state of the phase-1 pipeline of one CTA.
@@ -284,7 +289,7 @@ struct Pipe {
 
 template <int BX, int BY, int NCW, int SPW, int CB>
 __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, int tsplit,
-                              char *smem, unsigned int *bstat, Pipe &pp, volatile int *s_abort)
+                              char *smem, Pipe &pp, volatile int *s_abort)
 {
     using C = Cfg<BX, BY, NCW, SPW>;
     const int nbx = (pb.W + BX - 1) / BX;
@@ -336,7 +341,7 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
         const int nch = c1 - c0;
         if (warp == NCW) {
             // ---------------- producer warp ----------------
-            const uint32_t tx = (uint32_t)(C::WIN + nround) * kChunk;
+            const uint32_t tx = (uint32_t)C::WIN * kChunk;
             for (int k = 0; k < nch; ++k) {
                 const unsigned g = pp.g + k, st = g & 1u, use = g >> 1;
                 const bool ok = use < 1 || mbar_wait(&pp.empty[st], (use - 1) & 1u);
@@ -368,20 +373,27 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
                                  &pp.full[st]);
                     }
                 }
-                for (int sl = lane; sl < nround; sl += 32)
-                    bulk_g2s(dst + (size_t)(C::WIN + sl) * kChunk,
-                             chunk_ptr(pb, slots[base + sl].partner, c), kChunk, &pp.full[st]);
                 pp.issued = g + 1;
             }
         } else {
             // ---------------- compute warps ----------------
             int acc[SPW][kNCls];
             int corr[SPW];
+            uint32_t kq_next[SPW];
+            const uint32_t *prow[SPW];  // partner's count words, lane's column, chunk 0
 #pragma unroll
             for (int k = 0; k < SPW; ++k) {
                 corr[k] = 0;
 #pragma unroll
                 for (int c = 0; c < kNCls; ++c) acc[k][c] = 0;
+                const int sl = warp + k * NCW;
+                prow[k] = nullptr;
+                kq_next[k] = 0u;
+                if (sl < nround) {
+                    prow[k] = reinterpret_cast<const uint32_t *>(
+                                  chunk_ptr(pb, slots[base + sl].partner, 0)) + lane;
+                    kq_next[k] = __ldcg(prow[k] + (size_t)c0 * pb.P * kChunkWords);
+                }
             }
             for (int k = 0; k < nch; ++k) {
                 const unsigned g = pp.g + k, st = g & 1u, use = g >> 1;
@@ -394,10 +406,12 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
                 for (int q = 0; q < SPW; ++q) {
                     const int sl = warp + q * NCW;
                     if (sl < nround) {
+                        const uint32_t kq = kq_next[q];
+                        if (k + 1 < nch)
+                            kq_next[q] = __ldcg(prow[q] + (size_t)(c0 + k + 1) * pb.P * kChunkWords);
                         const int centre_idx = slots[base + sl].centre;
                         const uint32_t *centre = win + (size_t)centre_idx * kChunkWords + lane;
                         const uint32_t kp = *centre;
-                        const uint32_t kq = win[(size_t)(C::WIN + sl) * kChunkWords + lane];
                         const uint32_t d = sub_word<CB>(kq, kp);
                         corr[q] = dot_word<CB>(d, kq, corr[q]);
                         stencil_dot<CB, C::WINW>(centre, d, acc[q],
@@ -420,16 +434,6 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
                 const int sum = transpose_reduce32(v, lane);
                 int *dst = pb.side_cls + ((size_t)s.j * parts + s.side * tsplit + tpart) * kMaxClasses;
                 if (lane < kNCls) dst[lane] = sum;
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) {
-                    const int arrived = atomicAdd(pb.arrivals + s.j, 1);
-                    if (arrived == parts - 1) {
-                        __threadfence();
-                        pb.arrivals[s.j] = 0;
-                        finalize_couple(pb, s.j, sw, tsplit, bstat);
-                    }
-                }
             }
         }
         pp.g += nch;
@@ -454,15 +458,7 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
         if (ap < pb.P) prev[ap] = 0ull;
         if (bp < pb.P) prev[bp] = 0ull;
     }
-    if (a >= pb.P || b >= pb.P) {
-        if (lane == 0) {
-            pb.log_dE[j] = 0.f;
-            pb.log_flags[j] = 0;
-            pb.log_couples[2 * j] = a;
-            pb.log_couples[2 * j + 1] = b;
-        }
-        return false;
-    }
+    if (a >= pb.P || b >= pb.P) return false;  // logged by phase 2
     const uint8_t flags =
         (uint8_t)(__ldcg(reinterpret_cast<const unsigned int *>(pb.log_flags + (j & ~3))) >>
                   (8 * (j & 3)));
@@ -471,13 +467,22 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
     if (pb.mode == 0) {
         const unsigned long long key = couple_key(pb, sw, j);
         const unsigned long long *own = pb.owner + (size_t)(sw & 1u) * pb.P;
-        bool lose = false;
-        for (int i = lane; i < 2 * pb.n_off; i += 32) {
-            const int side = i >= pb.n_off;
-            const int p = side ? b : a;
-            const int q = neighbour(pb, p % pb.W, p / pb.W, side ? i - pb.n_off : i);
-            if (__ldcg(own + q) > key) lose = true;
+        const int ax = a % pb.W, ay = a / pb.W, bx = b % pb.W, by = b / pb.W;
+        constexpr int kPer = (2 * kNOff + 31) / 32;
+        unsigned long long v[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = lane + 32 * k;
+            v[k] = 0ull;
+            if (i < 2 * kNOff) {
+                const int side = i >= kNOff;
+                const int q = side ? neighbour(pb, bx, by, i - kNOff) : neighbour(pb, ax, ay, i);
+                v[k] = __ldcg(own + q);
+            }
         }
+        bool lose = false;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) lose |= v[k] > key;
         win = !__any_sync(0xFFFFFFFFu, lose);
     }
     if (!win) return false;
@@ -503,7 +508,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
     extern __shared__ __align__(128) char smem[];
     __shared__ int s_err, s_unit;
     __shared__ int s_abort;
-    __shared__ unsigned int bstat[4];
     const int nblocks = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (C::NT / 32) + warp, nwarps = nblocks * (C::NT / 32);
@@ -534,16 +538,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
             const int pi = find_problem(args.unit_start, args.n_prob, u);
             const Problem &pb = args.probs[pi];
             const long long s = pb.ctr[0] + it;
-            if (s < pb.ctr[1]) {
-                if (threadIdx.x < 4) bstat[threadIdx.x] = 0u;
-                __syncthreads();
+            if (s < pb.ctr[1])
                 evaluate_unit<BX, BY, NCW, SPW, CB>(pb, u - __ldg(args.unit_start + pi),
-                                                    (uint32_t)s, args.tsplit, smem, bstat, pp,
-                                                    &s_abort);
-                __syncthreads();
-                if (threadIdx.x < 4 && bstat[threadIdx.x])
-                    atomicAdd(&pb.stats[threadIdx.x], (unsigned long long)bstat[threadIdx.x]);
-            }
+                                                    (uint32_t)s, args.tsplit, smem, pp, &s_abort);
             const int ab = s_abort;
             __syncthreads();
             if (ab) break;
@@ -553,8 +550,36 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
             break;
         }
         if (!grid_sync(args.bar, nblocks, &s_err)) break;
-        // ---- phase 2: resolve + commit -------------------------------------------------------
+        // ---- phase 2: finalize (one thread per couple) ---------------------------------------
         if (blockIdx.x == 0 && threadIdx.x == 0) args.work[(it + 1) & 1] = 0;
+        for (int base = gwarp * 32; base < args.total_couples; base += nwarps * 32) {
+            const int g = base + lane;
+            int pi = -1;
+            uint8_t f = 0;
+            if (g < args.total_couples) {
+                pi = find_problem(args.couple_start, args.n_prob, g);
+                const Problem &pb = args.probs[pi];
+                const long long s = pb.ctr[0] + it;
+                if (s < pb.ctr[1])
+                    f = finalize_couple(pb, g - __ldg(args.couple_start + pi), (uint32_t)s,
+                                        args.tsplit);
+                else
+                    pi = -1;
+            }
+            // warp-aggregated counters, one group of lanes per problem
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, pi);
+            const unsigned nv = __popc(__ballot_sync(0xFFFFFFFFu, f & kFlagValid) & grp);
+            const unsigned ni = __popc(__ballot_sync(0xFFFFFFFFu, f & kFlagImproving) & grp);
+            const unsigned nt = __popc(__ballot_sync(0xFFFFFFFFu, f & kFlagTie) & grp);
+            if (pi >= 0 && lane == __ffs(grp) - 1) {
+                unsigned long long *st = args.probs[pi].stats;
+                if (nv) atomicAdd(&st[kStatValid], (unsigned long long)nv);
+                if (ni) atomicAdd(&st[kStatImproving], (unsigned long long)ni);
+                if (nt) atomicAdd(&st[kStatTies], (unsigned long long)nt);
+            }
+        }
+        if (!grid_sync(args.bar, nblocks, &s_err)) break;
+        // ---- phase 3: resolve + commit -------------------------------------------------------
         int cur_pi = -1;
         unsigned int mine = 0u;
         for (int g = gwarp; g < args.total_couples; g += nwarps) {
