@@ -188,14 +188,14 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
 
 /* ---- execution schedule (speed only; results do not depend on it) ------------------------ */
 /* kind: BN_SCHEDULE_*.  For the persistent kernel, block_x x block_y pixels per work unit,
- * threads per CTA and proposed pixels per warp per round must name an instantiated shape
- * (16x8/512/4, 8x16/512/4, 8x8/256/4); tsplit = chunk ranges per block (1..4, 0 = auto).
+ * threads per CTA and proposed pixels per compute warp per round must name an instantiated
+ * shape (16x8/512/4, 8x16/512/4, 8x8/256/4); tsplit = chunk ranges per block (1..4, 0 = auto).
  * block_x = 0 keeps the default shape.  set synchronises the stream. */
 typedef struct bn_schedule {
     int32_t kind;
     int32_t block_x, block_y;
     int32_t threads;
-    int32_t slots_per_warp;
+    int32_t slots_per_warp;   /* proposed pixels per compute warp per round */
     int32_t tsplit;
 } bn_schedule;
 int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc);

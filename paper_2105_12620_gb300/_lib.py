@@ -60,7 +60,7 @@ class BnSchedule(ctypes.Structure):
                 ("slots_per_warp", ctypes.c_int32), ("tsplit", ctypes.c_int32)]
 
 
-# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, slots/warp)
+# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, pixels/warp)
 PERSISTENT_SHAPES = [(16, 8, 512, 4), (8, 16, 512, 4), (8, 8, 256, 4)]
 
 

@@ -9,8 +9,10 @@
 //     the weight radius, wrapped on the torus) and each proposed pixel's partner chunk into a
 //     two-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion on
 //     an mbarrier); the counts are stored chunk-major, so every window row is one or two
-//     contiguous runs.  The compute warps read their proposed pixels' partner chunks straight
-//     from L2 (prefetched one chunk ahead) and accumulate, per proposed pixel p and class c,
+//     contiguous runs.  The producer runs one unit ahead: it publishes the next unit's proposed
+//     pixels while the compute warps still work on the current one.  The compute warps read
+//     their proposed pixels' partner chunks straight from L2 (prefetched one chunk ahead) and
+//     accumulate, per proposed pixel p and class c,
 //         A_c(p) += delta_p . k_q  over q in S_c(p),   delta_p = k_partner - k_p,
 //     with the 112 stencil offsets as compile-time shared-memory displacements (one IDP4A per
 //     four 8-bit counts).  The partner's own term is removed and the 18 class sums are reduced
@@ -118,6 +120,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
         if (clock64() - t0 > kBarrierSpinCycles) return false;
     return true;
 }
+// warp-uniform bounded wait that first honours an abort raised elsewhere in the CTA
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *s_abort)
+{
+    const int lane = threadIdx.x & 31;
+    bool ok = __shfl_sync(0xFFFFFFFFu, lane == 0 ? *s_abort : 0, 0) == 0;
+    if (ok) ok = __all_sync(0xFFFFFFFFu, mbar_wait(bar, parity));
+    if (!ok && lane == 0) *s_abort = 1;
+    return ok;
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
@@ -204,12 +215,24 @@ __device__ __forceinline__ int transpose_reduce32(int (&v)[32], int lane)
     return v[0];
 }
 
+
 struct Slot {
     int centre;   // window index of the pixel
     int j;        // couple
     int side;     // 0 = a, 1 = b
     int partner;  // partner pixel
     int cstar;    // class of the partner if it lies in the neighbourhood, else -1
+    int p;        // the pixel
+};
+
+// one work unit as published by the producer to the compute warps
+struct UnitHdr {
+    int nslot;    // -1: no more units in this pass
+    int pi;       // problem
+    int tpart;
+    int c0, c1;   // chunk range
+    uint32_t sw;  // pass index of the problem
+    int pad[2];
 };
 
 template <int BX, int BY, int NCW, int SPW>
@@ -221,9 +244,9 @@ struct Cfg {
     static constexpr int MAXSLOT = BX * BY;
     static constexpr int STAGE = WIN * kChunk;
     static constexpr int OFF_SLOTS = 2 * STAGE;
-    static constexpr int OFF_BAR = (OFF_SLOTS + MAXSLOT * (int)sizeof(Slot) + 63) / 64 * 64;
-    static constexpr int OFF_MISC = OFF_BAR + 64;
-    static constexpr size_t SMEM = (size_t)OFF_MISC + 64;
+    static constexpr int OFF_HDR = OFF_SLOTS + 2 * MAXSLOT * (int)sizeof(Slot);
+    static constexpr int OFF_BAR = (OFF_HDR + 2 * (int)sizeof(UnitHdr) + 63) / 64 * 64;
+    static constexpr size_t SMEM = (size_t)OFF_BAR + 128;  // 8 mbarriers
 };
 
 // finish a couple after phase 1: fp32 dL, flags, log, owner claim (one thread); returns flags
@@ -279,79 +302,115 @@ __device__ uint8_t finalize_couple(const Problem &pb, int j, uint32_t sw, int ts
     return flags;
 }
 
-// Shared state of the phase-1 pipeline of one CTA.
+// Per-CTA pipeline state.  Stage and slot-buffer use counters advance identically in every warp.
 struct Pipe {
-    uint64_t *full;   // [2] copies of a stage have landed
-    uint64_t *empty;  // [2] every compute warp is done with a stage
-    unsigned g;       // chunks streamed by this CTA so far (stage = g & 1)
-    unsigned issued;  // stage uses armed by the producer (for the abort path)
+    uint64_t *full;    // [2] copies of a stage have landed
+    uint64_t *empty;   // [2] every compute warp is done with a stage
+    uint64_t *sfull;   // [2] a unit's slot list and header are ready
+    uint64_t *sempty;  // [2] every compute warp is done with a slot list
+    unsigned g;        // chunks streamed so far (stage = g & 1)
+    unsigned ub;       // unit slot buffers used so far (buffer = ub & 1)
+    unsigned issued;   // stage uses armed by the producer (for the abort path)
 };
 
-template <int BX, int BY, int NCW, int SPW, int CB>
-__device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, int tsplit,
-                              char *smem, Pipe &pp, volatile int *s_abort)
+// Producer warp: takes units from the counter, publishes each unit's proposed pixels, then
+// streams the unit's window chunks (and the proposed pixels' partner chunks) into the ring.
+template <int BX, int BY, int NCW, int SPW>
+__device__ void produce_pass(const PersistentArgs &args, int it, char *smem, Pipe &pp,
+                             volatile int *s_abort)
 {
     using C = Cfg<BX, BY, NCW, SPW>;
-    const int nbx = (pb.W + BX - 1) / BX;
-    const int tpart = local_unit % tsplit;
-    const int blk = local_unit / tsplit;
-    const int x0 = (blk % nbx) * BX, y0 = (blk / nbx) * BY;
-    const int nchunks = pb.row_bytes / kChunk;
-    const int c0 = (int)((long long)nchunks * tpart / tsplit);
-    const int c1 = (int)((long long)nchunks * (tpart + 1) / tsplit);
-
-    Slot *slots = reinterpret_cast<Slot *>(smem + C::OFF_SLOTS);
-    int *s_nslot = reinterpret_cast<int *>(smem + C::OFF_MISC);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // 1. proposed pixels of the block
-    if (threadIdx.x == 0) *s_nslot = 0;
-    __syncthreads();
-    const uint32_t xs = pass_xor(pb, sw);
-    const int twoM = 2 * pb.M;
-    for (int lp = threadIdx.x; lp < BX * BY; lp += C::NT) {
-        const int x = x0 + lp % BX, y = y0 + lp / BX;
-        if (x >= pb.W || y >= pb.H) continue;
-        const int p = y * pb.W + x;
-        const int i = __ldg(pb.perm_inv + ((uint32_t)p ^ xs));
-        if (i >= twoM) continue;
-        const int partner = (int)((uint32_t)__ldg(pb.perm + (i ^ 1)) ^ xs);
-        if (partner >= pb.P) continue;
-        Slot s;
-        s.centre = (lp / BX + kR) * C::WINW + (lp % BX + kR);
-        s.j = i >> 1;
-        s.side = i & 1;
-        s.partner = partner;
-        const int ox = wrapi(partner % pb.W - x, pb.W), oy = wrapi(partner / pb.W - y, pb.H);
-        const int dx = min(ox, pb.W - ox), dy = min(oy, pb.H - oy);
-        const int d2 = dx * dx + dy * dy;
-        s.cstar = -1;
-        for (int c = 0; c < kNCls; ++c)
-            if (pb.d2[c] == d2) s.cstar = c;
-        slots[atomicAdd(s_nslot, 1)] = s;
-    }
-    __syncthreads();
-    const int nslot = *s_nslot;
-    if (nslot == 0) return;
-    const int parts = 2 * tsplit;
-    const int xa = x0 - kR, xb = x0 + BX + kR;  // window columns [xa, xb), W >= xb - xa
-
-    for (int base = 0; base < nslot; base += C::CAP) {
-        const int nround = min(C::CAP, nslot - base);
-        const int nch = c1 - c0;
-        if (warp == NCW) {
-            // ---------------- producer warp ----------------
-            const uint32_t tx = (uint32_t)C::WIN * kChunk;
-            for (int k = 0; k < nch; ++k) {
-                const unsigned g = pp.g + k, st = g & 1u, use = g >> 1;
-                const bool ok = use < 1 || mbar_wait(&pp.empty[st], (use - 1) & 1u);
-                if (!__all_sync(0xFFFFFFFFu, ok)) {
-                    if (lane == 0) *s_abort = 1;
-                    break;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(args.work + (it & 1), 1);
+        u = __shfl_sync(0xFFFFFFFFu, u, 0);
+        const unsigned b = pp.ub & 1u, buse = pp.ub >> 1;
+        int pi = -1;
+        long long s = 0;
+        if (u < args.total_units) {
+            pi = find_problem(args.unit_start, args.n_prob, u);
+            s = args.probs[pi].ctr[0] + it;
+            if (s >= args.probs[pi].ctr[1]) continue;  // problem already at its pass end
+        }
+        // the slot buffer must have been released by the compute warps
+        if (buse >= 1 && !warp_wait(&pp.sempty[b], (buse - 1) & 1u, s_abort)) return;
+        UnitHdr *hdr = reinterpret_cast<UnitHdr *>(smem + C::OFF_HDR) + b;
+        Slot *slots = reinterpret_cast<Slot *>(smem + C::OFF_SLOTS) + b * C::MAXSLOT;
+        if (pi < 0) {
+            if (lane == 0) {
+                hdr->nslot = -1;
+                mbar_arrive(&pp.sfull[b]);
+            }
+            ++pp.ub;
+            return;
+        }
+        const Problem &pb = args.probs[pi];
+        const int tsplit = args.tsplit;
+        const int lu = u - __ldg(args.unit_start + pi);
+        const int nbx = (pb.W + BX - 1) / BX;
+        const int tpart = lu % tsplit, blk = lu / tsplit;
+        const int x0 = (blk % nbx) * BX, y0 = (blk / nbx) * BY;
+        const int nchunks = pb.row_bytes / kChunk;
+        const int c0 = (int)((long long)nchunks * tpart / tsplit);
+        const int c1 = (int)((long long)nchunks * (tpart + 1) / tsplit);
+        const uint32_t sw = (uint32_t)s;
+        const uint32_t xs = pass_xor(pb, sw);
+        const int twoM = 2 * pb.M;
+        // proposed pixels, compacted in row-major order
+        int nslot = 0;
+        for (int base = 0; base < BX * BY; base += 32) {
+            const int lp = base + lane;
+            const int x = x0 + lp % BX, y = y0 + lp / BX;
+            bool hit = false;
+            Slot sl;
+            if (lp < BX * BY && x < pb.W && y < pb.H) {
+                const int p = y * pb.W + x;
+                const int i = __ldg(pb.perm_inv + ((uint32_t)p ^ xs));
+                if (i < twoM) {
+                    const int partner = (int)((uint32_t)__ldg(pb.perm + (i ^ 1)) ^ xs);
+                    if (partner < pb.P) {
+                        hit = true;
+                        sl.centre = (lp / BX + kR) * C::WINW + (lp % BX + kR);
+                        sl.j = i >> 1;
+                        sl.side = i & 1;
+                        sl.partner = partner;
+                        sl.p = p;
+                        const int ox = wrapi(partner % pb.W - x, pb.W);
+                        const int oy = wrapi(partner / pb.W - y, pb.H);
+                        const int dx = min(ox, pb.W - ox), dy = min(oy, pb.H - oy);
+                        const int d2 = dx * dx + dy * dy;
+                        sl.cstar = -1;
+                        for (int c = 0; c < kNCls; ++c)
+                            if (pb.d2[c] == d2) sl.cstar = c;
+                    }
                 }
-                if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? *s_abort : 0, 0)) break;
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, hit);
+            if (hit) slots[nslot + __popc(m & ((1u << lane) - 1u))] = sl;
+            nslot += __popc(m);
+        }
+        if (lane == 0) {
+            hdr->nslot = nslot;
+            hdr->pi = pi;
+            hdr->tpart = tpart;
+            hdr->c0 = c0;
+            hdr->c1 = c1;
+            hdr->sw = sw;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pp.sfull[b]);
+        ++pp.ub;
+        // stream the unit, one round of proposed pixels at a time
+        const int xa = x0 - kR, xb = x0 + BX + kR;  // window columns [xa, xb), W >= xb - xa
+        for (int base = 0; base < nslot; base += C::CAP) {
+            const int nround = min(C::CAP, nslot - base);
+            const uint32_t tx = (uint32_t)C::WIN * kChunk;
+            for (int c = c0; c < c1; ++c) {
+                const unsigned g = pp.g, st = g & 1u, use = g >> 1;
+                if (use >= 1 && !warp_wait(&pp.empty[st], (use - 1) & 1u, s_abort)) return;
+                if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? *s_abort : 0, 0)) return;
                 char *dst = smem + st * C::STAGE;
-                const int c = c0 + k;
                 if (lane == 0) mbar_arrive_expect_tx(&pp.full[st], tx);
                 __syncwarp();
                 for (int wy = lane; wy < C::WINH; wy += 32) {
@@ -374,16 +433,41 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
                     }
                 }
                 pp.issued = g + 1;
+                ++pp.g;
             }
-        } else {
-            // ---------------- compute warps ----------------
+        }
+    }
+}
+
+// Compute warps: for every unit of the pass and every round of its proposed pixels, warp w
+// accumulates the proposed pixels w, w + NCW, ... over the unit's chunks, then stores the class
+// sums of each (the partner's own term removed).
+template <int BX, int BY, int NCW, int SPW, int CB>
+__device__ void consume_pass(const PersistentArgs &args, char *smem, Pipe &pp,
+                             volatile int *s_abort)
+{
+    using C = Cfg<BX, BY, NCW, SPW>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        const unsigned b = pp.ub & 1u, buse = pp.ub >> 1;
+        if (!warp_wait(&pp.sfull[b], buse & 1u, s_abort)) return;
+        const UnitHdr hdr = reinterpret_cast<const UnitHdr *>(smem + C::OFF_HDR)[b];
+        const Slot *slots = reinterpret_cast<const Slot *>(smem + C::OFF_SLOTS) + b * C::MAXSLOT;
+        if (hdr.nslot < 0) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pp.sempty[b]);
+            ++pp.ub;
+            return;
+        }
+        const Problem &pb = args.probs[hdr.pi];
+        const int parts = 2 * args.tsplit;
+        for (int base = 0; base < hdr.nslot; base += C::CAP) {
+            const int nround = min(C::CAP, hdr.nslot - base);
             int acc[SPW][kNCls];
-            int corr[SPW];
             uint32_t kq_next[SPW];
-            const uint32_t *prow[SPW];  // partner's count words, lane's column, chunk 0
+            const uint32_t *prow[SPW];  // the partner's words of this lane, chunk 0
 #pragma unroll
             for (int k = 0; k < SPW; ++k) {
-                corr[k] = 0;
 #pragma unroll
                 for (int c = 0; c < kNCls; ++c) acc[k][c] = 0;
                 const int sl = warp + k * NCW;
@@ -392,57 +476,65 @@ __device__ void evaluate_unit(const Problem &pb, int local_unit, uint32_t sw, in
                 if (sl < nround) {
                     prow[k] = reinterpret_cast<const uint32_t *>(
                                   chunk_ptr(pb, slots[base + sl].partner, 0)) + lane;
-                    kq_next[k] = __ldcg(prow[k] + (size_t)c0 * pb.P * kChunkWords);
+                    kq_next[k] = __ldcg(prow[k] + (size_t)hdr.c0 * pb.P * kChunkWords);
                 }
             }
-            for (int k = 0; k < nch; ++k) {
-                const unsigned g = pp.g + k, st = g & 1u, use = g >> 1;
-                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&pp.full[st], use & 1u))) {
-                    if (lane == 0) *s_abort = 1;
-                    break;
-                }
+            for (int c = hdr.c0; c < hdr.c1; ++c) {
+                const unsigned g = pp.g, st = g & 1u, use = g >> 1;
+                if (!warp_wait(&pp.full[st], use & 1u, s_abort)) return;
                 const uint32_t *win = reinterpret_cast<const uint32_t *>(smem + st * C::STAGE);
 #pragma unroll
-                for (int q = 0; q < SPW; ++q) {
-                    const int sl = warp + q * NCW;
+                for (int k = 0; k < SPW; ++k) {
+                    const int sl = warp + k * NCW;
                     if (sl < nround) {
-                        const uint32_t kq = kq_next[q];
-                        if (k + 1 < nch)
-                            kq_next[q] = __ldcg(prow[q] + (size_t)(c0 + k + 1) * pb.P * kChunkWords);
-                        const int centre_idx = slots[base + sl].centre;
-                        const uint32_t *centre = win + (size_t)centre_idx * kChunkWords + lane;
-                        const uint32_t kp = *centre;
-                        const uint32_t d = sub_word<CB>(kq, kp);
-                        corr[q] = dot_word<CB>(d, kq, corr[q]);
-                        stencil_dot<CB, C::WINW>(centre, d, acc[q],
+                        const uint32_t kq = kq_next[k];
+                        if (c + 1 < hdr.c1)
+                            kq_next[k] = __ldcg(prow[k] + (size_t)(c + 1) * pb.P * kChunkWords);
+                        const uint32_t *centre =
+                            win + (size_t)slots[base + sl].centre * kChunkWords + lane;
+                        const uint32_t d = sub_word<CB>(kq, *centre);
+                        stencil_dot<CB, C::WINW>(centre, d, acc[k],
                                                  std::make_integer_sequence<int, kNOff>{});
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&pp.empty[st]);
+                ++pp.g;
             }
-            // publish: per slot, the 18 class sums of this side and chunk range
 #pragma unroll
-            for (int q = 0; q < SPW; ++q) {
-                const int sl = warp + q * NCW;
+            for (int k = 0; k < SPW; ++k) {
+                const int sl = warp + k * NCW;
                 if (sl >= nround) continue;
                 const Slot s = slots[base + sl];
+                // rare: the partner lies in the neighbourhood; remove its own term, recomputed
+                // from the counts over the unit's chunks
+                int corr = 0;
+                if (s.cstar >= 0) {
+                    for (int c = hdr.c0; c < hdr.c1; ++c) {
+                        const uint32_t kq = __ldcg(reinterpret_cast<const unsigned int *>(
+                                                       chunk_ptr(pb, s.partner, c)) + lane);
+                        const uint32_t kp = __ldcg(reinterpret_cast<const unsigned int *>(
+                                                       chunk_ptr(pb, s.p, c)) + lane);
+                        corr = dot_word<CB>(sub_word<CB>(kq, kp), kq, corr);
+                    }
+                }
                 int v[32];
 #pragma unroll
                 for (int c = 0; c < 32; ++c)
-                    v[c] = c < kNCls ? acc[q][c] - (c == s.cstar ? corr[q] : 0) : 0;
+                    v[c] = c < kNCls ? acc[k][c] - (c == s.cstar ? corr : 0) : 0;
                 const int sum = transpose_reduce32(v, lane);
-                int *dst = pb.side_cls + ((size_t)s.j * parts + s.side * tsplit + tpart) * kMaxClasses;
-                if (lane < kNCls) dst[lane] = sum;
+                if (lane < kNCls)
+                    pb.side_cls[((size_t)s.j * parts + s.side * args.tsplit + hdr.tpart) *
+                                    kMaxClasses + lane] = sum;
             }
         }
-        pp.g += nch;
-        __syncthreads();
-        if (*s_abort) return;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pp.sempty[b]);
+        ++pp.ub;
     }
 }
 
-// phase 2 for one couple (one warp); returns true (on lane 0) when the swap was applied
+// phase 3 for one couple (one warp); returns true (on lane 0) when the swap was applied
 __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
 {
     const int lane = threadIdx.x & 31;
@@ -506,7 +598,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
 {
     using C = Cfg<BX, BY, NCW, SPW>;
     extern __shared__ __align__(128) char smem[];
-    __shared__ int s_err, s_unit;
+    __shared__ int s_err;
     __shared__ int s_abort;
     const int nblocks = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -515,13 +607,18 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
     Pipe pp;
     pp.full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
     pp.empty = pp.full + 2;
+    pp.sfull = pp.full + 4;
+    pp.sempty = pp.full + 6;
     pp.g = 0;
+    pp.ub = 0;
     pp.issued = 0;
     if (threadIdx.x == 0) {
-        mbar_init(&pp.full[0], 1);
-        mbar_init(&pp.full[1], 1);
-        mbar_init(&pp.empty[0], NCW);
-        mbar_init(&pp.empty[1], NCW);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&pp.full[i], 1);
+            mbar_init(&pp.empty[i], NCW);
+            mbar_init(&pp.sfull[i], 1);
+            mbar_init(&pp.sempty[i], NCW);
+        }
         mbar_init_fence();
         s_abort = 0;
         s_err = 0;
@@ -530,21 +627,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
 
     for (int it = 0; it < args.n_iter; ++it) {
         // ---- phase 1: evaluate (units from an atomic counter) -------------------------------
-        for (;;) {
-            if (threadIdx.x == 0) s_unit = atomicAdd(args.work + (it & 1), 1);
-            __syncthreads();
-            const int u = s_unit;
-            if (u >= args.total_units) break;
-            const int pi = find_problem(args.unit_start, args.n_prob, u);
-            const Problem &pb = args.probs[pi];
-            const long long s = pb.ctr[0] + it;
-            if (s < pb.ctr[1])
-                evaluate_unit<BX, BY, NCW, SPW, CB>(pb, u - __ldg(args.unit_start + pi),
-                                                    (uint32_t)s, args.tsplit, smem, pp, &s_abort);
-            const int ab = s_abort;
-            __syncthreads();
-            if (ab) break;
-        }
+        if (warp == NCW)
+            produce_pass<BX, BY, NCW, SPW>(args, it, smem, pp, &s_abort);
+        else
+            consume_pass<BX, BY, NCW, SPW, CB>(args, smem, pp, &s_abort);
+        __syncthreads();
         if (s_abort) {
             if (threadIdx.x == 0) atomicExch(&args.bar->error, 2u);
             break;
@@ -680,10 +767,11 @@ cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &sh
                               int sms, cudaStream_t st)
 {
     cudaError_t e = cudaErrorInvalidValue;
-#define BN_SHAPE(BX, BY, NCW, SPW, MINB)                                                      \
-    if (shape.bx == BX && shape.by == BY && shape.threads == (NCW + 1) * 32 && shape.spw == SPW) \
-        e = cb == 1 ? launch_cfg<BX, BY, NCW, SPW, 1, MINB>(a, sms, st)                      \
-                    : launch_cfg<BX, BY, NCW, SPW, 2, MINB>(a, sms, st);
+#define BN_SHAPE(BX, BY, NCW, KMAX, MINB)                                                     \
+    if (shape.bx == BX && shape.by == BY && shape.threads == (NCW + 1) * 32 &&                \
+        shape.spw == KMAX)                                                                     \
+        e = cb == 1 ? launch_cfg<BX, BY, NCW, KMAX, 1, MINB>(a, sms, st)                     \
+                    : launch_cfg<BX, BY, NCW, KMAX, 2, MINB>(a, sms, st);
     BN_PERSISTENT_SHAPES(BN_SHAPE)
 #undef BN_SHAPE
     note_launches(1);

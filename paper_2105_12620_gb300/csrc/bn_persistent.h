@@ -35,8 +35,8 @@ struct PersistentShape {
     int bx, by, threads, spw, tsplit;
 };
 
-// Instantiated CTA shapes: X(bx, by, compute warps, slots per warp per round, min CTAs per SM);
-// every CTA has one more warp, the producer (threads = 32 * (compute warps + 1)).
+// Instantiated CTA shapes: X(bx, by, compute warps, proposed pixels per warp per round, min
+// CTAs per SM); every CTA has one more warp, the producer (threads = 32 * (compute warps + 1)).
 #define BN_PERSISTENT_SHAPES(X) \
     X(16, 8, 15, 4, 1)          \
     X(8, 16, 15, 4, 1)          \
