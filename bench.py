@@ -228,6 +228,10 @@ def run_ours(args) -> int:
                          sigma=SIGMA, radius=RADIUS, schedule=schedule, stream=stream)
              for i in range(B)]
     batch = pkg.Batch(tiles, stream=stream) if B > 1 else None
+    chosen = None
+    if args.schedule == "auto":
+        # untimed: trial passes on a scratch copy pick the CTA shape / chunk split
+        chosen = batch.autotune(20) if batch is not None else tiles[0].autotune(20)
     shifts_dev = torch.empty((B, H_TILE, W_TILE, 2), dtype=torch.float32, device="cuda")
     energy_dev = torch.empty((B,), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -329,7 +333,12 @@ def run_ours(args) -> int:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "tiles_per_gpu": B, "sweeps": args.sweeps,
-                       "schedule": args.schedule, "parallelism": f"independent tiles x{world}",
+                       "schedule": args.schedule if chosen is None else
+                       {"kind": "persistent" if chosen["kind"] == pkg.BN_SCHEDULE_PERSISTENT
+                        else "plain", "block": chosen["shape"][:2],
+                        "threads": chosen["shape"][2], "tsplit": chosen["tsplit"],
+                        "chosen_by": "autotuner"},
+                       "parallelism": f"independent tiles x{world}",
                        "l2": "flushed between steps (256 MB write)"},
             "tiles_per_s": world * B * args.steps / (total_ms / 1000.0),
             "e2e": {"value": e2e_value, "unit": UNIT,

@@ -201,6 +201,14 @@ typedef struct bn_schedule {
 int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc);
 int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out);
 
+/* Autotuner: time every instantiated schedule (CTA shape x chunk split, plain as fallback) for
+ * trial_sweeps passes on a scratch copy of the device state, keep the fastest, and cache the
+ * choice per workload signature (tile sizes, N, T, couples, radius, SM count) in the process and,
+ * when the environment variable BN_AUTOTUNE_CACHE names a file, in that file.  The caller's
+ * tiles are not modified; results never depend on the schedule.  chosen: nullable.
+ * Synchronises. */
+int bn_sampler_autotune(bn_sampler *s, int32_t trial_sweeps, bn_schedule *chosen);
+
 /* ---- batches: many samplers swept together in one launch sequence ------------------------- */
 typedef struct bn_batch bn_batch;
 
@@ -210,6 +218,7 @@ typedef struct bn_batch bn_batch;
 int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out);
 int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats);
 int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc);
+int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen);
 int bn_batch_get_schedule(bn_batch *b, bn_schedule *out);
 void bn_batch_destroy(bn_batch *b);
 

@@ -2,6 +2,9 @@
 // device memory, problem descriptors, and the call sequences of init / sweeps / fetches.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -767,6 +770,8 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
     return BN_OK;
 }
 
+}  // extern "C"
+
 static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Problem *dprob,
                                const bn_schedule *sc, SweepPlan &plan)
 {
@@ -799,6 +804,201 @@ static void get_schedule_common(const SweepPlan &pl, bn_schedule *out)
     out->tsplit = pl.shape.tsplit;
 }
 
+// ---- autotuner: choose the execution schedule of a problem list by timing trial passes -----
+// Trials run on a scratch copy of the members' device state (one device-to-device copy of each
+// member's slab, descriptors rebased onto it), so the caller's tiles are untouched; since every
+// schedule produces bit-identical results, the choice only affects speed.  Choices are cached
+// per process by workload signature and, when BN_AUTOTUNE_CACHE names a file, in that file.
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, bn_schedule> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(const std::vector<bn::Problem> &hp, int sms)
+{
+    std::string k = "sm" + std::to_string(sms);
+    for (const auto &h : hp)
+        k += "|" + std::to_string(h.W) + "x" + std::to_string(h.H) + "n" + std::to_string(h.N) +
+             "t" + std::to_string(h.T) + "m" + std::to_string(h.M) + "r" + std::to_string(h.radius);
+    return k;
+}
+
+void tune_file_load()
+{
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char *path = std::getenv("BN_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[8192];
+    bn_schedule sc{};
+    while (std::fscanf(f, "%8191s %d %d %d %d %d %d", key, &sc.kind, &sc.block_x, &sc.block_y,
+                       &sc.threads, &sc.slots_per_warp, &sc.tsplit) == 7)
+        g_tune_cache[key] = sc;
+    std::fclose(f);
+}
+
+void tune_file_store(const std::string &key, const bn_schedule &sc)
+{
+    const char *path = std::getenv("BN_AUTOTUNE_CACHE");
+    if (!path || key.size() > 8000) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), sc.kind, sc.block_x, sc.block_y,
+                 sc.threads, sc.slots_per_warp, sc.tsplit);
+    std::fclose(f);
+}
+
+void rebase(bn::Problem &h, const char *from, char *to)
+{
+    auto mv = [&](auto *&p) {
+        if (p) p = reinterpret_cast<std::remove_reference_t<decltype(p)>>(
+                   to + (reinterpret_cast<const char *>(p) - from));
+    };
+    mv(h.counts); mv(h.U); mv(h.sidx); mv(h.perm); mv(h.perm_inv); mv(h.ha); mv(h.hb);
+    mv(h.hC); mv(h.owner); mv(h.log_dE); mv(h.log_flags); mv(h.log_couples);
+    mv(h.side_cls); mv(h.ctr); mv(h.stats); mv(h.esum); mv(h.energy_out);
+}
+
+// Time every candidate schedule on a scratch copy of the members; returns the fastest.
+int autotune(const std::vector<bn_sampler *> &members, int32_t trial_sweeps, cudaStream_t st,
+             bn_schedule *best)
+{
+    // scratch copy, problems grouped by count width as in a batch
+    std::vector<char *> clones(members.size(), nullptr);
+    std::vector<bn::Problem> hp;
+    bn::Problem *dp = nullptr;
+    SweepPlan plan;
+    int rc = BN_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        for (char *c : clones)
+            if (c) cudaFree(c);
+        if (dp) cudaFree(dp);
+        free_plan(plan);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    for (size_t i = 0; i < members.size(); ++i) {
+        cudaError_t e = cudaMalloc(&clones[i], members[i]->slab_bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(clones[i], members[i]->slab, members[i]->slab_bytes,
+                                cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            cleanup();
+            return fail(e == cudaErrorMemoryAllocation ? BN_ERR_OOM : BN_ERR_CUDA,
+                        "autotune scratch copy failed: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int cb = 1; cb <= 2; ++cb)
+        for (size_t i = 0; i < members.size(); ++i)
+            for (auto h : members[i]->hprob)
+                if (h.count_bytes == cb) {
+                    rebase(h, members[i]->slab, clones[i]);
+                    hp.push_back(h);
+                }
+    cudaError_t e = cudaMalloc(&dp, sizeof(bn::Problem) * hp.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dp, hp.data(), sizeof(bn::Problem) * hp.size(),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(BN_ERR_CUDA, "autotune setup failed: %s", cudaGetErrorString(e));
+    }
+    std::vector<bn_schedule> cands;
+#define BN_CAND(BX, BY, NCW, SPW, MINB)                                                        \
+    for (int ts = 1; ts <= 2; ++ts) cands.push_back(bn_schedule{BN_SCHEDULE_PERSISTENT, BX, BY,   \
+                                                                (NCW + 1) * 32, SPW, ts});
+    BN_PERSISTENT_SHAPES(BN_CAND)
+#undef BN_CAND
+    cands.push_back(bn_schedule{BN_SCHEDULE_PLAIN, 0, 0, 0, 0, 0});
+    float best_ms = -1.f;
+    for (const auto &c : cands) {
+        bn::PersistentShape shape{c.block_x, c.block_y, c.threads, c.slots_per_warp, c.tsplit};
+        bool fits = c.kind == BN_SCHEDULE_PLAIN;
+        if (!fits) {
+            fits = true;
+            for (const auto &h : hp)
+                fits = fits && bn::persistent_shape_fits(h, shape) && h.row_bytes / 128 >= c.tsplit;
+        }
+        if (!fits) continue;
+        if (c.kind == BN_SCHEDULE_PLAIN && best_ms >= 0.f) continue;  // plain only as fallback
+        if ((rc = make_plan(hp, dp, c.kind, c.kind == BN_SCHEDULE_PLAIN ? nullptr : &shape, plan)))
+            break;
+        if ((rc = run_plan(plan, dp, hp, 2, st, nullptr))) break;  // warm
+        cudaEventRecord(e0, st);
+        if ((rc = run_plan(plan, dp, hp, trial_sweeps, st, nullptr))) break;
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = fail(BN_ERR_CUDA, "autotune trial failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cleanup();
+    if (rc) return rc;
+    if (best_ms < 0.f) return fail(BN_ERR_BAD_STATE, "autotune found no runnable schedule");
+    return BN_OK;
+}
+
+int autotune_entry(const std::vector<bn_sampler *> &members, const std::vector<bn::Problem> &hp,
+                   const bn::Problem *dprob, cudaStream_t st, int32_t trial_sweeps,
+                   SweepPlan &plan, bn_schedule *chosen)
+{
+    if (trial_sweeps < 1 || trial_sweeps > 10000)
+        return fail(BN_ERR_INVALID_ARG, "trial_sweeps must be in [1, 10000]");
+    int dev = 0, sms = 0;
+    BN_CUDA(cudaGetDevice(&dev));
+    BN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const std::string key = tune_key(hp, sms);
+    bn_schedule best{};
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_file_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            hit = true;
+        }
+    }
+    if (!hit) {
+        for (auto *m : members) BN_CUDA(cudaStreamSynchronize(m->stream));
+        if (int rc = autotune(members, trial_sweeps, st, &best)) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+        tune_file_store(key, best);
+    }
+    if (int rc = set_schedule_common(hp, dprob, &best, plan)) return rc;
+    if (chosen) *chosen = best;
+    return BN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bn_sampler_autotune(bn_sampler *s, int32_t trial_sweeps, bn_schedule *chosen)
+{
+    if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
+    if (int rc = set_device(s)) return rc;
+    if (int rc = autotune_entry({s}, s->hprob, s->dprob, s->stream, trial_sweeps, s->plan, chosen))
+        return rc;
+    s->schedule = s->plan.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    return BN_OK;
+}
+
 int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc)
 {
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
@@ -821,6 +1021,12 @@ int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc)
     if (!b) return fail(BN_ERR_INVALID_ARG, "null batch");
     BN_CUDA(cudaStreamSynchronize(b->stream));
     return set_schedule_common(b->all, b->dprob, sc, b->plan);
+}
+
+int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen)
+{
+    if (!b) return fail(BN_ERR_INVALID_ARG, "null batch");
+    return autotune_entry(b->members, b->all, b->dprob, b->stream, trial_sweeps, b->plan, chosen);
 }
 
 int bn_batch_get_schedule(bn_batch *b, bn_schedule *out)

@@ -110,6 +110,11 @@ class Sampler:
         L.check(L.load().bn_sampler_get_schedule(self._h, ctypes.byref(sc)))
         return _unpack(sc)
 
+    def autotune(self, trial_sweeps: int = 20) -> dict:
+        sc = L.BnSchedule()
+        L.check(L.load().bn_sampler_autotune(self._h, trial_sweeps, ctypes.byref(sc)))
+        return _unpack(sc)
+
     def reset(self, seed: int) -> None:
         L.check(L.load().bn_sampler_reset(self._h, seed))
 
@@ -199,6 +204,11 @@ class Batch:
     def get_schedule(self) -> dict:
         sc = L.BnSchedule()
         L.check(L.load().bn_batch_get_schedule(self._h, ctypes.byref(sc)))
+        return _unpack(sc)
+
+    def autotune(self, trial_sweeps: int = 20) -> dict:
+        sc = L.BnSchedule()
+        L.check(L.load().bn_batch_autotune(self._h, trial_sweeps, ctypes.byref(sc)))
         return _unpack(sc)
 
     def close(self) -> None:

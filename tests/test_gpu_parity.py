@@ -278,3 +278,29 @@ def test_persistent_batch_equals_each_alone(pkg):
     b.close()
     for m in mixed:
         m.close()
+
+
+def test_autotune_leaves_state_alone_and_keeps_results(pkg):
+    cfgs = [(48, 40, 16, 128, 1), (64, 64, 64, 256, 1), (40, 40, 256, 128, 2)]
+    tiles = [pkg.Sampler(W, H, N, T, seed=W * 7 + H, n_pairs=p) for W, H, N, T, p in cfgs]
+    for t in tiles:
+        t.optimize(5, stats=False)
+    before = [(t.shifts(), t.counts(0), t.get_state()[0]) for t in tiles]
+    b = pkg.Batch(tiles)
+    chosen = b.autotune(4)
+    assert chosen["kind"] in (pkg.BN_SCHEDULE_PERSISTENT, pkg.BN_SCHEDULE_PLAIN)
+    for t, (sh, k, sw) in zip(tiles, before):
+        assert np.array_equal(t.shifts(), sh) and np.array_equal(t.counts(0), k)
+        assert t.get_state()[0] == sw
+    assert b.autotune(4) == chosen          # cached
+    b.optimize(20, stats=False)
+    refs = [pkg.Sampler(W, H, N, T, seed=W * 7 + H, n_pairs=p, schedule=pkg.BN_SCHEDULE_PLAIN)
+            for W, H, N, T, p in cfgs]
+    for r in refs:
+        r.optimize(25, stats=False)
+    for t, r in zip(tiles, refs):
+        assert np.array_equal(t.shifts(), r.shifts())
+        r.close()
+    b.close()
+    for t in tiles:
+        t.close()
