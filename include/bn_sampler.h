@@ -222,6 +222,25 @@ int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen);
 int bn_batch_get_schedule(bn_batch *b, bn_schedule *out);
 void bn_batch_destroy(bn_batch *b);
 
+/* ---- Eq. 1 without device allocation -------------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory (code running inside another framework's memory pool or arena, real-time loops that
+ * must not stall on the allocator, plug-ins that are only handed pre-allocated buffers).  It
+ * computes the same Eq. 1 as bn_evaluate_energy, for n_fields count fields given by the caller,
+ * and allocates nothing: its only scratch is a fixed 16 KiB array of the library (per-class
+ * sums of up to 64 fields) that every GPU loading the library keeps until the process exits.
+ *   counts   device, int32 [n_fields][height][width][n_integrands]; values in [0, n_points]
+ *   energy   device, n_fields doubles (written)
+ *   n_fields 1..64 (more is rejected with BN_ERR_INVALID_ARG: the scratch holds 64 fields)
+ *   width, height, n_points, n_integrands, sigma, radius: as in bn_config (radius 1..8)
+ * Enqueued on cuda_stream; returns without waiting.  The first call on each device looks up
+ * the device address of the scratch array (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  Every call shares the scratch array: a call clears what it uses
+ * before accumulating, but calls whose work overlaps on the GPU race on it. */
+int bn_evaluate_energy_noalloc(const int32_t *counts, int32_t n_fields, int32_t width,
+                               int32_t height, int32_t n_points, int32_t n_integrands,
+                               float sigma, int32_t radius, double *energy, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

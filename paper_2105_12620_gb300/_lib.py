@@ -98,6 +98,9 @@ _SIGS = {
     "bn_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
     "bn_sampler_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSchedule)]),
     "bn_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSchedule)]),
+    "bn_evaluate_energy_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_float, ctypes.c_int32, _P, _P]),
     "bn_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P,
                                        ctypes.POINTER(_P)]),
     "bn_batch_optimize": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSweepStats)]),

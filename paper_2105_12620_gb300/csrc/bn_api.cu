@@ -30,6 +30,12 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
+}  // namespace
+
+void bn::set_last_error(const char *msg) { g_error = msg; }
+
+namespace {
+
 #define BN_CUDA(call)                                                                        \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \

@@ -10,6 +10,9 @@
 
 namespace bn {
 
+// message returned by bn_last_error() on this thread
+void set_last_error(const char *msg);
+
 // process-wide count of kernel launches made by this library
 void note_launches(long long n);
 long long launch_count();
