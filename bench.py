@@ -229,7 +229,14 @@ def run_ours(args) -> int:
              for i in range(B)]
     batch = pkg.Batch(tiles, stream=stream) if B > 1 else None
     chosen = None
-    if args.schedule == "auto":
+    if args.block:
+        bx, by = (int(v) for v in args.block.split("x"))
+        for obj in ([batch] if batch is not None else tiles):
+            obj.set_schedule(pkg.BN_SCHEDULE_PERSISTENT, (bx, by, args.threads, args.spw),
+                             args.tsplit)
+        chosen = (batch if batch is not None else tiles[0]).get_schedule()
+        chosen["chosen_by"] = "command line"
+    elif args.schedule == "auto":
         # untimed: trial passes on a scratch copy pick the CTA shape / chunk split
         chosen = batch.autotune(20) if batch is not None else tiles[0].autotune(20)
     shifts_dev = torch.empty((B, H_TILE, W_TILE, 2), dtype=torch.float32, device="cuda")
@@ -337,7 +344,7 @@ def run_ours(args) -> int:
                        {"kind": "persistent" if chosen["kind"] == pkg.BN_SCHEDULE_PERSISTENT
                         else "plain", "block": chosen["shape"][:2],
                         "threads": chosen["shape"][2], "tsplit": chosen["tsplit"],
-                        "chosen_by": "autotuner"},
+                        "chosen_by": chosen.get("chosen_by", "autotuner")},
                        "parallelism": f"independent tiles x{world}",
                        "l2": "flushed between steps (256 MB write)"},
             "tiles_per_s": world * B * args.steps / (total_ms / 1000.0),
@@ -374,6 +381,10 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--block", default="", help="force a persistent CTA block, e.g. 8x8")
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--spw", type=int, default=4)
+    ap.add_argument("--tsplit", type=int, default=1)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -170,6 +170,13 @@ int bn_fetch_sweep_log(bn_sampler *s, int32_t pair, float *dE, uint8_t *flags,
 int bn_get_state(bn_sampler *s, int64_t *sweep, int32_t *shift_index, size_t n);
 int bn_set_state(bn_sampler *s, int64_t sweep, const int32_t *shift_index, size_t n);
 
+/* Self-test of the kernels' bounded waits: runs the grid barrier (which = 0, waiting for one
+ * more block than exists) or an mbarrier wait (which = 1, nobody arrives) with a budget of
+ * budget_cycles SM clock cycles (1000 .. 2^31) on a condition that cannot occur.  Returns
+ * BN_ERR_TIMEOUT when the wait gave up and reported it, as it must; the GPU context stays
+ * usable.  Synchronises the legacy default stream. */
+int bn_selftest_wait_timeout(int32_t which, int64_t budget_cycles);
+
 /* Number of kernels this library has launched in this process (all samplers). */
 int64_t bn_launch_counter(void);
 

@@ -88,6 +88,7 @@ _SIGS = {
     "bn_set_state": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_size_t]),
     "bn_evaluate_energy_device": (ctypes.c_int, [_P, _P]),
     "bn_launch_counter": (ctypes.c_int64, []),
+    "bn_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
     "bn_sampler_reset": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "bn_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "bn_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(BnKernelTime), ctypes.c_int32,

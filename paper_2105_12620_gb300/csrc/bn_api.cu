@@ -291,6 +291,20 @@ int set_device(const bn_sampler *s)
     return BN_OK;
 }
 
+// A bounded device-side wait that ran out leaves a sticky error in the problems' counters; the
+// synchronous calls report it.  The sampler's stream must be synchronised.
+int check_device_error(const bn_sampler *s)
+{
+    for (const auto &h : s->hprob) {
+        unsigned long long err = 0;
+        BN_CUDA(cudaMemcpy(&err, h.stats + bn::kStatError, sizeof err, cudaMemcpyDeviceToHost));
+        if (err)
+            return fail(BN_ERR_TIMEOUT, "a device-side wait ran out (code %llu); the sampler's "
+                        "state is undefined, reset it", err);
+    }
+    return BN_OK;
+}
+
 // Build the execution plan of a problem list (grouped by count width, 1-byte group first).
 // schedule: BN_SCHEDULE_*; the persistent schedule needs the radius-6 stencil on tiles of at
 // least 13 x 13 for every problem.
@@ -421,6 +435,7 @@ int run_plan(const SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn
             if (e != cudaSuccess)
                 return fail(BN_ERR_CUDA, "persistent launch (%dx%d, %d threads) failed: %s",
                             pl.shape.bx, pl.shape.by, pl.shape.threads, cudaGetErrorString(e));
+            BN_CUDA(bn::launch_fold_error(pl.d_bar, a.probs, a.n_prob, st));
         }
     }
     (void)hp;
@@ -537,6 +552,7 @@ int bn_evaluate_energy(bn_sampler *s, double *energy_per_pair)
         BN_CUDA(cudaMemcpyAsync(s->h_energy + i, s->hprob[i].energy_out, sizeof(double),
                                 cudaMemcpyDeviceToHost, s->stream));
     BN_CUDA(cudaStreamSynchronize(s->stream));
+    if (int rc = check_device_error(s)) return rc;
     for (int i = 0; i < s->n_prob; ++i) energy_per_pair[i] = s->h_energy[i];
     return BN_OK;
 }
@@ -551,6 +567,28 @@ int bn_evaluate_energy_device(bn_sampler *s, double *energy_per_pair_device)
 }
 
 int64_t bn_launch_counter(void) { return (int64_t)bn::launch_count(); }
+
+int bn_selftest_wait_timeout(int32_t which, int64_t budget_cycles)
+{
+    if (which != 0 && which != 1) return fail(BN_ERR_INVALID_ARG, "which must be 0 or 1");
+    if (budget_cycles < 1000 || budget_cycles > (1ll << 31))
+        return fail(BN_ERR_INVALID_ARG, "budget_cycles must be in [1000, 2^31]");
+    bn::GridBarrier *gb = nullptr;
+    int *res = nullptr;
+    int host = -1;
+    cudaError_t e = cudaMalloc(&gb, sizeof *gb);
+    if (e == cudaSuccess) e = cudaMalloc(&res, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(gb, 0, sizeof *gb);
+    if (e == cudaSuccess) e = cudaMemset(res, 0xFF, sizeof(int));
+    if (e == cudaSuccess) e = bn::launch_selftest_wait(which, budget_cycles, gb, res, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&host, res, sizeof(int), cudaMemcpyDeviceToHost);
+    if (gb) cudaFree(gb);
+    if (res) cudaFree(res);
+    if (e != cudaSuccess) return fail(BN_ERR_CUDA, "self-test launch failed: %s", cudaGetErrorString(e));
+    if (host == 1) return fail(BN_ERR_TIMEOUT, "the wait ran out as expected");
+    if (host == 0) return BN_OK;
+    return fail(BN_ERR_BAD_STATE, "self-test produced no result");
+}
 
 }  // extern "C"
 
@@ -604,6 +642,7 @@ int bn_fetch_shifts(bn_sampler *s, float *out, size_t n_floats, int out_is_devic
         BN_CUDA(cudaMemcpyAsync(s->h_shifts, s->d_shifts, sizeof(float) * per * s->n_prob,
                                 cudaMemcpyDeviceToHost, s->stream));
         BN_CUDA(cudaStreamSynchronize(s->stream));
+        if (int rc = check_device_error(s)) return rc;
         memcpy(out, s->h_shifts, sizeof(float) * per * s->n_prob);
     }
     return BN_OK;
@@ -696,6 +735,7 @@ int bn_get_state(bn_sampler *s, int64_t *sweep, int32_t *shift_index, size_t n)
             BN_CUDA(cudaMemcpyAsync(shift_index + P * i, s->hprob[i].sidx, sizeof(int32_t) * P,
                                     cudaMemcpyDeviceToHost, s->stream));
     BN_CUDA(cudaStreamSynchronize(s->stream));
+    if (int rc = check_device_error(s)) return rc;
     if (sweep) *sweep = s->sweep;
     return BN_OK;
 }

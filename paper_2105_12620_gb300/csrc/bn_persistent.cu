@@ -112,12 +112,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 // bounded wait: false when the clock budget runs out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          long long budget = kBarrierSpinCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kBarrierSpinCycles) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 // warp-uniform bounded wait that first honours an abort raised elsewhere in the CTA
@@ -139,7 +140,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // ---- grid barrier (bounded spin) ----------------------------------------------------------
-__device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned int nblocks, int *s_err)
+__device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned int nblocks, int *s_err,
+                                          long long budget = kBarrierSpinCycles)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -155,7 +157,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned int nblocks,
             const long long t0 = clock64();
             while (*gen == g) {
                 if (*err) break;
-                if (clock64() - t0 > kBarrierSpinCycles) {
+                if (clock64() - t0 > budget) {
                     atomicExch(&gb->error, 1u);
                     break;
                 }
@@ -721,6 +723,40 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
     }
 }
 
+// after a persistent launch: a barrier timeout or an aborted pipeline becomes a sticky error of
+// every problem of the launch (read back as BN_ERR_TIMEOUT)
+__global__ void k_fold_error(const GridBarrier *gb, const Problem *probs, int n_prob)
+{
+    const unsigned int err = gb->error;
+    if (!err) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_prob; i += gridDim.x * blockDim.x)
+        atomicOr(&probs[i].stats[kStatError], (unsigned long long)err);
+}
+
+// Runs the kernel's own bounded waits on conditions that cannot occur, with a short budget:
+// which = 0: a grid barrier that waits for one more block than the grid has;
+// which = 1: an mbarrier that nobody arrives at.  result[0] = 1 when the wait ran out.
+__global__ void k_selftest_wait(int which, long long budget, GridBarrier *gb, int *result)
+{
+    __shared__ int s_err;
+    __shared__ uint64_t bar;
+    bool ok;
+    if (which == 0) {
+        if (threadIdx.x == 0) s_err = 0;
+        __syncthreads();
+        ok = grid_sync(gb, gridDim.x + 1u, &s_err, budget);
+    } else {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        ok = mbar_wait(&bar, 0u, budget);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) result[0] = ok ? 0 : 1;
+}
+
 template <int BX, int BY, int NCW, int SPW, int CB, int MINB>
 cudaError_t launch_cfg(const PersistentArgs &a0, int sms, cudaStream_t st)
 {
@@ -761,6 +797,22 @@ bool persistent_shape_fits(const Problem &h, const PersistentShape &s)
 {
     // a window row must wrap at most once
     return persistent_supported(h) && h.W >= s.bx + 2 * kR;
+}
+
+cudaError_t launch_fold_error(const GridBarrier *gb, const Problem *probs, int n_prob,
+                              cudaStream_t st)
+{
+    k_fold_error<<<1, 128, 0, st>>>(gb, probs, n_prob);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_wait(int which, long long budget, GridBarrier *gb, int *result,
+                                 cudaStream_t st)
+{
+    k_selftest_wait<<<which == 0 ? 2 : 1, 64, 0, st>>>(which, budget, gb, result);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &shape, int cb,

@@ -47,5 +47,9 @@ bool persistent_supported(const Problem &h);
 bool persistent_shape_fits(const Problem &h, const PersistentShape &s);
 cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &shape, int cb,
                               int sms, cudaStream_t st);
+cudaError_t launch_fold_error(const GridBarrier *gb, const Problem *probs, int n_prob,
+                              cudaStream_t st);
+cudaError_t launch_selftest_wait(int which, long long budget, GridBarrier *gb, int *result,
+                                 cudaStream_t st);
 
 }  // namespace bn

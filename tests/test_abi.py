@@ -75,3 +75,8 @@ def test_null_arguments(lib):
     assert lib.bn_optimize_sweeps(None, 1, None) == L.BN_ERR_INVALID_ARG
     assert lib.bn_fetch_shifts(None, None, 0, 0) == L.BN_ERR_INVALID_ARG
     lib.bn_sampler_destroy(None)
+
+
+def test_selftest_arguments_validated_on_the_host(lib):
+    assert lib.bn_selftest_wait_timeout(2, 1 << 20) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_selftest_wait_timeout(0, 10) == L.BN_ERR_INVALID_ARG

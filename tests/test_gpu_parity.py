@@ -304,3 +304,17 @@ def test_autotune_leaves_state_alone_and_keeps_results(pkg):
     b.close()
     for t in tiles:
         t.close()
+
+
+def test_bounded_waits_report_timeouts_and_the_context_survives(pkg):
+    """The kernels' grid barrier and mbarrier waits give up after their clock budget and report
+    it (no trap, no hang); afterwards the GPU context is still usable."""
+    from paper_2105_12620_gb300 import _lib as L
+    lib = L.load()
+    for which in (0, 1):
+        assert lib.bn_selftest_wait_timeout(which, 1 << 22) == L.BN_ERR_TIMEOUT
+        assert "ran out" in lib.bn_last_error().decode()
+    s = pkg.Sampler(32, 32, 16, 64, seed=1)
+    st = s.optimize(3)
+    assert st.sweeps == 3 and st.proposals > 0
+    s.close()
