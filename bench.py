@@ -375,7 +375,7 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--tiles", type=int, default=16, help="tiles per GPU per step")
+    ap.add_argument("--tiles", type=int, default=32, help="tiles per GPU per step")
     ap.add_argument("--sweeps", type=int, default=SWEEPS)
     ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto")
     ap.add_argument("--cpu-sweeps", type=int, default=20)

@@ -251,12 +251,22 @@ struct Cfg {
     static constexpr size_t SMEM = (size_t)OFF_BAR + 128;  // 8 mbarriers
 };
 
-// finish a couple after phase 1: fp32 dL, flags, log, owner claim (one thread); returns flags
+// finish a couple after phase 1: fp32 dL, flags, log, owner claim (one thread); returns flags.
+// Also clears the couple's claims of the previous pass (the other parity of the owner grid,
+// read by the previous pass's phase 3 and next written by the next pass's phase 2).
 __device__ uint8_t finalize_couple(const Problem &pb, int j, uint32_t sw, int tsplit)
 {
+    const int pj0 = __ldg(pb.perm + 2 * j), pj1 = __ldg(pb.perm + 2 * j + 1);
+    if (sw > 0 && pb.mode == 0) {
+        const uint32_t xp = pass_xor(pb, sw - 1u);
+        const int ap = (int)((uint32_t)pj0 ^ xp), bp = (int)((uint32_t)pj1 ^ xp);
+        unsigned long long *prev = pb.owner + (size_t)((sw - 1u) & 1u) * pb.P;
+        if (ap < pb.P) prev[ap] = 0ull;
+        if (bp < pb.P) prev[bp] = 0ull;
+    }
     const uint32_t xs = pass_xor(pb, sw);
-    const int a = (int)((uint32_t)__ldg(pb.perm + 2 * j) ^ xs);
-    const int b = (int)((uint32_t)__ldg(pb.perm + 2 * j + 1) ^ xs);
+    const int a = (int)((uint32_t)pj0 ^ xs);
+    const int b = (int)((uint32_t)pj1 ^ xs);
     pb.log_couples[2 * j] = a;
     pb.log_couples[2 * j + 1] = b;
     if (a >= pb.P || b >= pb.P) {
@@ -536,28 +546,14 @@ __device__ void consume_pass(const PersistentArgs &args, char *smem, Pipe &pp,
     }
 }
 
-// phase 3 for one couple (one warp); returns true (on lane 0) when the swap was applied
-__device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
+// phase 3 for one improving couple (one warp): keep it unless an interacting improving couple
+// has a higher priority, then swap; returns true (on every lane) when the swap was applied
+__device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw, uint8_t flags)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t xs = pass_xor(pb, sw);
     const int a = (int)((uint32_t)__ldg(pb.perm + 2 * j) ^ xs);
     const int b = (int)((uint32_t)__ldg(pb.perm + 2 * j + 1) ^ xs);
-    // owner claims of the previous pass (same parity as the next one) are cleared here
-    if (sw > 0 && pb.mode == 0 && lane == 0) {
-        const uint32_t xp = pass_xor(pb, sw - 1u);
-        const int ap = (int)((uint32_t)__ldg(pb.perm + 2 * j) ^ xp);
-        const int bp = (int)((uint32_t)__ldg(pb.perm + 2 * j + 1) ^ xp);
-        unsigned long long *prev = pb.owner + (size_t)((sw - 1u) & 1u) * pb.P;
-        if (ap < pb.P) prev[ap] = 0ull;
-        if (bp < pb.P) prev[bp] = 0ull;
-    }
-    if (a >= pb.P || b >= pb.P) return false;  // logged by phase 2
-    const uint8_t flags =
-        (uint8_t)(__ldcg(reinterpret_cast<const unsigned int *>(pb.log_flags + (j & ~3))) >>
-                  (8 * (j & 3)));
-    if (!(flags & kFlagImproving)) return false;
-    bool win = true;
     if (pb.mode == 0) {
         const unsigned long long key = couple_key(pb, sw, j);
         const unsigned long long *own = pb.owner + (size_t)(sw & 1u) * pb.P;
@@ -577,9 +573,8 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
         bool lose = false;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) lose |= v[k] > key;
-        win = !__any_sync(0xFFFFFFFFu, lose);
+        if (__any_sync(0xFFFFFFFFu, lose)) return false;
     }
-    if (!win) return false;
     for (int vi = lane; vi < (pb.row_bytes >> 4); vi += 32) {
         uint4 *pa = vec_ptr(pb, a, vi), *pbp = vec_ptr(pb, b, vi);
         const uint4 x = __ldcg(pa), y = __ldcg(pbp);
@@ -592,7 +587,7 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw)
         pb.sidx[b] = t;
         pb.log_flags[j] = flags | kFlagCommitted;
     }
-    return lane == 0;
+    return true;
 }
 
 template <int BX, int BY, int NCW, int SPW, int CB, int MINB>
@@ -669,23 +664,36 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
         }
         if (!grid_sync(args.bar, nblocks, &s_err)) break;
         // ---- phase 3: resolve + commit -------------------------------------------------------
-        int cur_pi = -1;
-        unsigned int mine = 0u;
-        for (int g = gwarp; g < args.total_couples; g += nwarps) {
-            const int pi = find_problem(args.couple_start, args.n_prob, g);
-            const Problem &pb = args.probs[pi];
-            const long long s = pb.ctr[0] + it;
-            if (s >= pb.ctr[1]) continue;
-            if (pi != cur_pi) {
-                if (cur_pi >= 0 && mine && lane == 0)
-                    atomicAdd(&args.probs[cur_pi].stats[kStatCommitted], (unsigned long long)mine);
-                mine = 0u;
-                cur_pi = pi;
+        // 32 couples per warp step: one flag load each, then the improving ones one by one
+        for (int base = gwarp * 32; base < args.total_couples; base += nwarps * 32) {
+            const int g = base + lane;
+            int pi = 0, j = 0;
+            uint8_t f = 0;
+            uint32_t sw = 0;
+            if (g < args.total_couples) {
+                pi = find_problem(args.couple_start, args.n_prob, g);
+                const Problem &pb = args.probs[pi];
+                const long long s = pb.ctr[0] + it;
+                if (s < pb.ctr[1]) {
+                    j = g - __ldg(args.couple_start + pi);
+                    sw = (uint32_t)s;
+                    f = (uint8_t)(__ldcg(reinterpret_cast<const unsigned int *>(pb.log_flags +
+                                                                               (j & ~3))) >>
+                                  (8 * (j & 3)));
+                }
             }
-            if (resolve_commit(pb, g - __ldg(args.couple_start + pi), (uint32_t)s)) mine += 1u;
+            unsigned m = __ballot_sync(0xFFFFFFFFu, (f & kFlagImproving) != 0);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1u;
+                const int lpi = __shfl_sync(0xFFFFFFFFu, pi, l);
+                const int lj = __shfl_sync(0xFFFFFFFFu, j, l);
+                const uint32_t lsw = __shfl_sync(0xFFFFFFFFu, sw, l);
+                const uint8_t lf = (uint8_t)__shfl_sync(0xFFFFFFFFu, (int)f, l);
+                if (resolve_commit(args.probs[lpi], lj, lsw, lf) && lane == 0)
+                    atomicAdd(&args.probs[lpi].stats[kStatCommitted], 1ull);
+            }
         }
-        if (cur_pi >= 0 && mine && lane == 0)
-            atomicAdd(&args.probs[cur_pi].stats[kStatCommitted], (unsigned long long)mine);
         if (!grid_sync(args.bar, nblocks, &s_err)) break;
     }
     if (s_abort || s_err) {
