@@ -197,6 +197,38 @@ def plain_per_tile(pkg, stream, rank, sweeps: int = 500, reps: int = 3) -> dict:
             "note": f"1 tile, plain schedule, {reps}x{sweeps} passes (no re-initialisation)"}
 
 
+def run_serving(pkg, args, rank: int, local: int, world: int, dist) -> dict:
+    """Bounded run of the serving loop: a Poisson stream of mixed requests per GPU (weak
+    scaling: every rank serves its own stream); latencies are the worst rank's."""
+    import torch
+
+    from paper_2105_12620_gb300 import serving as srv
+
+    reqs = srv.draw_requests(args.serving_requests, args.serving_rate, seed=1000 + rank)
+    with pkg.Server(max_slots=args.serving_slots, sweeps_per_chunk=args.serving_chunk,
+                    device=local) as sv:
+        summary = srv.run_load(sv, reqs, timeout_s=args.serving_timeout)
+        summary["server"] = sv.stats()
+    if dist is not None:
+        keys = ("p50_latency_s", "p99_latency_s", "makespan_s")
+        t = torch.tensor([summary[k] for k in keys], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        for k, v in zip(keys, t.tolist()):
+            summary[k] = v
+        tot = torch.tensor([summary["proposals_per_s"] * summary["makespan_s"],
+                            summary["completed"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tot)
+        summary["proposals_per_s"] = float(tot[0]) / summary["makespan_s"]
+        summary["served_req_per_s"] = float(tot[1]) / summary["makespan_s"]
+    summary["config"] = {
+        "stream": f"Poisson {args.serving_rate:g} req/s per GPU, {args.serving_requests} "
+                  "requests (bounded run), side log-uniform 32..512, N in {16,64,256}, T=1024, "
+                  "1 or 2 pairs, pass budget uniform 500..5000",
+        "max_slots": args.serving_slots, "sweeps_per_chunk": args.serving_chunk,
+        "memory_budget": "80% of free device memory", "latency": "submit to done"}
+    return summary
+
+
 def run_ours(args) -> int:
     import torch
 
@@ -327,6 +359,9 @@ def run_ours(args) -> int:
     plain = None
     if not args.no_plain and rank == 0:
         plain = plain_per_tile(pkg, stream, rank)
+    serving = None
+    if args.serving_requests > 0:
+        serving = run_serving(pkg, args, rank, local, world, dist)
     line = None
     if rank == 0:
         cpu = None
@@ -357,6 +392,7 @@ def run_ours(args) -> int:
             "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in ktimes.items()},
             "cpu_baseline": cpu,
             "plain_per_tile": plain,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if batch is not None:
@@ -385,6 +421,12 @@ def main(argv=None) -> int:
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--spw", type=int, default=4)
     ap.add_argument("--tsplit", type=int, default=1)
+    ap.add_argument("--serving-requests", type=int, default=64,
+                    help="requests of the bounded serving run (0 skips it)")
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrivals/s")
+    ap.add_argument("--serving-slots", type=int, default=64)
+    ap.add_argument("--serving-chunk", type=int, default=50)
+    ap.add_argument("--serving-timeout", type=float, default=300.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -220,14 +220,79 @@ int bn_sampler_autotune(bn_sampler *s, int32_t trial_sweeps, bn_schedule *chosen
 typedef struct bn_batch bn_batch;
 
 /* Group samplers (all created on the same device) so that their sweeps run fused: every pair
- * of every sampler becomes one problem of a single launch.  The batch uses its own stream
- * (cuda_stream) and records events to order itself after each member's stream. */
+ * of every sampler becomes one problem of a single launch.  The batch sweeps on its own stream
+ * (cuda_stream): a sweep call first waits for each member's stream to finish its queued work,
+ * and work enqueued later on a member's stream waits for the batch's sweeps (event). */
 int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out);
 int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats);
+/* As bn_batch_optimize, with a pass budget per member sampler (host array, one entry per sampler
+ * in the order given to bn_batch_create); members stop at their own budget inside the launch. */
+int bn_batch_optimize_each(bn_batch *b, const int32_t *n_sweeps_per_member,
+                           bn_sweep_stats *stats);
 int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc);
 int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen);
 int bn_batch_get_schedule(bn_batch *b, bn_schedule *out);
 void bn_batch_destroy(bn_batch *b);
+
+/* ---- serving: continuous batching of sampler-generation requests --------------------------
+ * The paper runs one optimisation at a time; this is the serving loop around it.  A server owns
+ * one GPU and a background host thread.  Each request is one sampler configuration plus a pass
+ * budget.  The thread admits queued requests (first come, first served) while a slot is free and
+ * their device memory fits the budget, initialises their samplers on a side stream, sweeps all
+ * resident requests together in fused batches of at most sweeps_per_chunk passes each (each
+ * request stops at its own budget inside the launch), and retires finished ones (final Eq. 1 and
+ * the optimised shifts copied to host, device memory released).  A request's result is identical
+ * to running it alone through bn_sampler_init + bn_optimize_sweeps with the same pass budget.
+ * All functions are thread-safe; none waits for the GPU except bn_server_drain/destroy. */
+typedef struct bn_server bn_server;
+
+typedef struct bn_server_config {
+    int32_t device;               /* CUDA device index                                       */
+    int32_t max_slots;            /* resident requests at most (1..4096)                     */
+    int32_t sweeps_per_chunk;     /* passes per fused launch sequence (1..500)               */
+    int32_t reserved;
+    int64_t memory_budget_bytes;  /* device bytes for resident requests; 0 = 80% of free     */
+} bn_server_config;
+
+typedef struct bn_request {
+    bn_config cfg;                /* the sampler to build (schedule is ignored)              */
+    int32_t n_sweeps;             /* pass budget (>= 1)                                      */
+    int32_t reserved;
+    int64_t user_tag;             /* returned unchanged in the result                        */
+} bn_request;
+
+typedef struct bn_result {
+    int64_t request_id, user_tag;
+    int32_t status;               /* BN_OK, BN_ERR_BAD_STATE when cancelled, else the error  */
+    int32_t n_pairs, width, height;
+    double energy[2];             /* Eq. 1 of each pair after the budget                     */
+    double t_submit, t_admit, t_done;  /* seconds since the server was created              */
+} bn_result;
+
+typedef struct bn_server_stats {
+    int64_t submitted, admitted, completed, rejected, cancelled, failed;
+    int64_t pending, active;      /* queued / resident right now                             */
+    int64_t chunks;               /* fused launch sequences run                              */
+    int64_t proposals;            /* couples proposed (pairs x couples x passes)             */
+    int64_t memory_in_use, memory_budget;
+} bn_server_stats;
+
+int bn_server_create(const bn_server_config *cfg, bn_server **out);
+/* Queue a request; request_id (nullable) receives its id.  BN_ERR_INVALID_ARG for an invalid
+ * configuration, BN_ERR_BUSY (counted as rejected) when it alone exceeds the memory budget. */
+int bn_server_submit(bn_server *sv, const bn_request *req, int64_t *request_id);
+/* Cancel a queued or resident request; it is reported with status BN_ERR_BAD_STATE. */
+int bn_server_cancel(bn_server *sv, int64_t request_id);
+/* Move up to cap finished results (in completion order) into out; *n_out = how many. */
+int bn_server_poll(bn_server *sv, bn_result *out, int32_t cap, int32_t *n_out);
+/* Copy a completed request's shifts (host floats [n_pairs][height][width][2], the layout of
+ * bn_fetch_shifts) and release them; each request's shifts can be taken once. */
+int bn_server_take_shifts(bn_server *sv, int64_t request_id, float *out, size_t n_floats);
+int bn_server_get_stats(bn_server *sv, bn_server_stats *out);
+/* Wait until no request is queued or resident (BN_ERR_BUSY at the timeout). */
+int bn_server_drain(bn_server *sv, double timeout_s);
+/* Stop the thread after its current chunk; resident and queued requests are dropped. */
+void bn_server_destroy(bn_server *sv);
 
 /* ---- Eq. 1 without device allocation -------------------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that cannot allocate device

@@ -7,4 +7,4 @@ The computation lives in ``libbnsampler.so`` (CUDA, sm_103a), reached through th
 from ._lib import (BN_MODE_CONCURRENT, BN_MODE_NONINTERACTING, BN_OBJECTIVE_BLUE,  # noqa: F401
                    BN_OBJECTIVE_LITERAL, BN_SCHEDULE_AUTO, BN_SCHEDULE_PERSISTENT,
                    BN_SCHEDULE_PLAIN, BnError, load)
-from .sampler import Batch, Sampler, SweepStats  # noqa: F401
+from .sampler import Batch, Result, Sampler, Server, SweepStats  # noqa: F401

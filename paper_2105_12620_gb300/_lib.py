@@ -60,8 +60,33 @@ class BnSchedule(ctypes.Structure):
                 ("slots_per_warp", ctypes.c_int32), ("tsplit", ctypes.c_int32)]
 
 
+class BnServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("sweeps_per_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("memory_budget_bytes", ctypes.c_int64)]
+
+
+class BnRequest(ctypes.Structure):
+    _fields_ = [("cfg", BnConfig), ("n_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("user_tag", ctypes.c_int64)]
+
+
+class BnResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("user_tag", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("n_pairs", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("energy", ctypes.c_double * 2), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class BnServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "admitted", "completed", "rejected", "cancelled", "failed", "pending",
+        "active", "chunks", "proposals", "memory_in_use", "memory_budget")]
+
+
 # CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, pixels/warp)
-PERSISTENT_SHAPES = [(16, 8, 512, 4), (8, 16, 512, 4), (8, 8, 256, 4)]
+PERSISTENT_SHAPES = [(8, 8, 256, 4), (16, 8, 512, 4), (8, 16, 512, 4)]
 
 
 class BnError(RuntimeError):
@@ -105,7 +130,18 @@ _SIGS = {
     "bn_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P,
                                        ctypes.POINTER(_P)]),
     "bn_batch_optimize": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSweepStats)]),
+    "bn_batch_optimize_each": (ctypes.c_int, [_P, _P, ctypes.POINTER(BnSweepStats)]),
     "bn_batch_destroy": (None, [_P]),
+    "bn_server_create": (ctypes.c_int, [ctypes.POINTER(BnServerConfig), ctypes.POINTER(_P)]),
+    "bn_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(BnRequest),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "bn_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "bn_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(BnResult), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "bn_server_take_shifts": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_size_t]),
+    "bn_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(BnServerStats)]),
+    "bn_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "bn_server_destroy": (None, [_P]),
 }
 
 _lib = None

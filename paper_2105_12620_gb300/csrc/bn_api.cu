@@ -103,7 +103,7 @@ namespace {
 // How the passes of a set of problems are executed, and the device arrays that go with it.
 struct SweepPlan {
     bool persistent = false;
-    bn::PersistentShape shape{16, 8, 512, 4, 0};
+    bn::PersistentShape shape{8, 8, 256, 4, 0};
     // per count width (index cb - 1): first problem, problem count, units / couples prefix
     int first[2] = {0, 0}, count[2] = {0, 0};
     int total_units[2] = {0, 0}, total_couples[2] = {0, 0};
@@ -146,12 +146,16 @@ struct bn_sampler {
 
 struct bn_batch {
     std::vector<bn_sampler *> members;
+    std::vector<int> member_of;        // member index of each problem (grouped order)
+    int *h_ends = nullptr;             // pinned, [n_prob] pass budgets
+    int *d_ends = nullptr;             // device copy
     cudaStream_t stream = nullptr;
     bn::Problem *dprob = nullptr;
     int n_prob = 0;
     int max_M = 0;
     int count_bytes = 1;
     bn::KernelTimer *timer = nullptr;  // the first member's timer
+    cudaEvent_t done = nullptr;        // end of the last sweep call, awaited by member streams
     std::vector<bn::Problem> all;      // host copies, grouped by count width
     SweepPlan plan;
 };
@@ -275,6 +279,24 @@ void carve(Slab &s, bn::Problem &h)
     h.esum = s.take<unsigned long long>(bn::kMaxClasses);
     h.energy_out = s.take<double>(1);
 }
+
+}  // namespace
+
+// device bytes a sampler of this configuration holds (slab + staging), without allocating
+int64_t bn::estimate_device_bytes(const bn_config &c)
+{
+    if (validate(c) != BN_OK) return -1;
+    Slab sizing;
+    for (int i = 0; i < c.n_pairs; ++i) {
+        bn::Problem h;
+        describe(c, i, h);
+        carve(sizing, h);
+    }
+    return (int64_t)(sizing.used + 256 + sizeof(bn::Problem) * c.n_pairs +
+                     sizeof(float) * (size_t)c.width * c.height * 2 * c.n_pairs + 4096);
+}
+
+namespace {
 
 int check_pair(bn_sampler *s, int32_t pair)
 {
@@ -401,9 +423,9 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
 constexpr int kItersPerLaunch = 500;
 
 int run_plan(const SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Problem> &hp,
-             int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm)
+             int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm, bool set_end = true)
 {
-    BN_CUDA(bn::launch_set_end(dprob, pl.n_prob, n_sweeps, 1, st));
+    if (set_end) BN_CUDA(bn::launch_set_end(dprob, pl.n_prob, n_sweeps, 1, st));
     if (!pl.persistent) {
         for (int g = 0; g < 2; ++g) {
             if (!pl.count[g]) continue;
@@ -1031,6 +1053,15 @@ int autotune_entry(const std::vector<bn_sampler *> &members, const std::vector<b
     return BN_OK;
 }
 
+// work that a member later enqueues on its own stream starts after the batch's last sweep call
+int order_members_after(bn_batch *b)
+{
+    BN_CUDA(cudaEventRecord(b->done, b->stream));
+    for (auto *m : b->members)
+        if (m->stream != b->stream) BN_CUDA(cudaStreamWaitEvent(m->stream, b->done, 0));
+    return BN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1069,6 +1100,30 @@ int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc)
     return set_schedule_common(b->all, b->dprob, sc, b->plan);
 }
 
+int bn_batch_optimize_each(bn_batch *b, const int32_t *n_sweeps_per_member,
+                           bn_sweep_stats *stats)
+{
+    if (!b || !n_sweeps_per_member) return fail(BN_ERR_INVALID_ARG, "null argument");
+    int32_t most = 0;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        if (n_sweeps_per_member[i] < 0) return fail(BN_ERR_INVALID_ARG, "negative pass count");
+        most = n_sweeps_per_member[i] > most ? n_sweeps_per_member[i] : most;
+    }
+    for (auto *m : b->members)
+        if (m->stream != b->stream) BN_CUDA(cudaStreamSynchronize(m->stream));
+    // the pinned staging may still feed the previous call's copy
+    BN_CUDA(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n_prob; ++i) b->h_ends[i] = n_sweeps_per_member[b->member_of[i]];
+    BN_CUDA(cudaMemcpyAsync(b->d_ends, b->h_ends, sizeof(int) * b->n_prob,
+                            cudaMemcpyHostToDevice, b->stream));
+    BN_CUDA(bn::launch_set_ends(b->dprob, b->n_prob, b->d_ends, 1, b->stream));
+    if (int rc = run_plan(b->plan, b->dprob, b->all, most, b->stream, b->timer, false)) return rc;
+    if (int rc = order_members_after(b)) return rc;
+    for (size_t i = 0; i < b->members.size(); ++i) b->members[i]->sweep += n_sweeps_per_member[i];
+    if (stats) return read_stats(b->all, b->stream, stats);
+    return BN_OK;
+}
+
 int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen)
 {
     if (!b) return fail(BN_ERR_INVALID_ARG, "null batch");
@@ -1097,7 +1152,10 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
                 return fail(BN_ERR_INVALID_ARG, "null sampler in batch");
             }
             for (auto &h : samplers[i]->hprob)
-                if (h.count_bytes == cb) all.push_back(h);
+                if (h.count_bytes == cb) {
+                    all.push_back(h);
+                    b->member_of.push_back(i);
+                }
         }
     for (int i = 0; i < n; ++i) b->members.push_back(samplers[i]);
     b->timer = &samplers[0]->timer;
@@ -1107,6 +1165,9 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
     if (e == cudaSuccess)
         e = cudaMemcpy(b->dprob, all.data(), sizeof(bn::Problem) * all.size(),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_ends, sizeof(int) * all.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ends, sizeof(int) * all.size());
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         bn_batch_destroy(b);
         return fail(BN_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
@@ -1133,6 +1194,7 @@ int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats)
         BN_CUDA(cudaStreamSynchronize(m->stream));
     }
     if (int rc = run_plan(b->plan, b->dprob, b->all, n_sweeps, b->stream, b->timer)) return rc;
+    if (int rc = order_members_after(b)) return rc;
     for (auto *m : b->members) m->sweep += n_sweeps;
     if (stats) return read_stats(b->all, b->stream, stats);
     return BN_OK;
@@ -1143,6 +1205,9 @@ void bn_batch_destroy(bn_batch *b)
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     if (b->dprob) cudaFree(b->dprob);
+    if (b->h_ends) cudaFreeHost(b->h_ends);
+    if (b->d_ends) cudaFree(b->d_ends);
+    if (b->done) cudaEventDestroy(b->done);
     free_plan(b->plan);
     delete b;
 }

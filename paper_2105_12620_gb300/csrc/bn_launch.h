@@ -7,8 +7,12 @@
 #include <cuda_runtime.h>
 
 #include "bn_device.cuh"
+#include "bn_sampler.h"
 
 namespace bn {
+
+// device bytes a sampler of this configuration would hold; -1 if the configuration is invalid
+int64_t estimate_device_bytes(const bn_config &c);
 
 // message returned by bn_last_error() on this thread
 void set_last_error(const char *msg);
@@ -66,5 +70,7 @@ struct SweepLaunch {
 cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm);
 cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int reset_stats,
                            cudaStream_t st);
+cudaError_t launch_set_ends(const Problem *dprob, int n_prob, const int *n_sweeps_dev,
+                            int reset_stats, cudaStream_t st);
 
 }  // namespace bn

@@ -38,9 +38,9 @@ struct PersistentShape {
 // Instantiated CTA shapes: X(bx, by, compute warps, proposed pixels per warp per round, min
 // CTAs per SM); every CTA has one more warp, the producer (threads = 32 * (compute warps + 1)).
 #define BN_PERSISTENT_SHAPES(X) \
+    X(8, 8, 7, 4, 2)            \
     X(16, 8, 15, 4, 1)          \
-    X(8, 16, 15, 4, 1)          \
-    X(8, 8, 7, 4, 2)
+    X(8, 16, 15, 4, 1)
 
 int persistent_units_per_problem(const Problem &h, int bx, int by, int tsplit);
 bool persistent_supported(const Problem &h);

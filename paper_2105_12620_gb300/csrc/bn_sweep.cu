@@ -217,7 +217,29 @@ __global__ void k_set_end(const Problem *probs, int n_sweeps, int reset_stats)
     if (reset_stats && threadIdx.x < kStatCount) pb.stats[threadIdx.x] = 0ull;
 }
 
+// per-problem pass budgets: ctr[1] = ctr[0] + n[i]
+__global__ void k_set_ends(const Problem *probs, int n_prob, const int *n_sweeps, int reset_stats)
+{
+    for (int i = blockIdx.x; i < n_prob; i += gridDim.x) {
+        const Problem &pb = probs[i];
+        if (threadIdx.x == 0) {
+            pb.ctr[1] = pb.ctr[0] + n_sweeps[i];
+            pb.ctr[2] = 0;
+        }
+        if (reset_stats && threadIdx.x < kStatCount) pb.stats[threadIdx.x] = 0ull;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_set_ends(const Problem *dprob, int n_prob, const int *n_sweeps_dev,
+                            int reset_stats, cudaStream_t st)
+{
+    k_set_ends<<<n_prob < 1024 ? n_prob : 1024, 32, 0, st>>>(dprob, n_prob, n_sweeps_dev,
+                                                             reset_stats);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int reset_stats,
                            cudaStream_t st)

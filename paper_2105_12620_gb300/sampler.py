@@ -197,6 +197,15 @@ class Batch:
             return None
         return SweepStats(st.sweeps, st.proposals, st.improving, st.committed, st.ties)
 
+    def optimize_each(self, n_sweeps_per_member, stats: bool = True) -> SweepStats | None:
+        arr = np.ascontiguousarray(n_sweeps_per_member, np.int32)
+        st = L.BnSweepStats()
+        L.check(L.load().bn_batch_optimize_each(self._h, arr.ctypes.data,
+                                                ctypes.byref(st) if stats else None))
+        if not stats:
+            return None
+        return SweepStats(st.sweeps, st.proposals, st.improving, st.committed, st.ties)
+
     def set_schedule(self, kind: int, shape=None, tsplit: int = 0) -> None:
         sc = _schedule(kind, shape, tsplit)
         L.check(L.load().bn_batch_set_schedule(self._h, ctypes.byref(sc)))
@@ -221,3 +230,83 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+@dataclass
+class Result:
+    request_id: int
+    user_tag: int
+    status: int
+    n_pairs: int
+    width: int
+    height: int
+    energy: tuple
+    t_submit: float
+    t_admit: float
+    t_done: float
+
+
+class Server:
+    """Continuous-batching server: requests (a tile configuration and a pass budget) are queued,
+    admitted under a slot and device-memory budget, swept together in fused chunks by a
+    background thread of the library, and retired with their final Eq. 1 and shifts."""
+
+    def __init__(self, max_slots: int = 64, sweeps_per_chunk: int = 50,
+                 memory_budget_bytes: int = 0, device: int = 0):
+        self.cfg = L.BnServerConfig(device, max_slots, sweeps_per_chunk, 0, memory_budget_bytes)
+        self._h = ctypes.c_void_p()
+        L.check(L.load().bn_server_create(ctypes.byref(self.cfg), ctypes.byref(self._h)))
+
+    def submit(self, width: int, height: int, n_points: int, n_integrands: int, n_sweeps: int,
+               seed: int = 0, n_pairs: int = 1, generator_g: int = 0, sigma: float = 2.1,
+               radius: int = 6, couples_per_sweep: int = 0,
+               mode: int = L.BN_MODE_NONINTERACTING, objective: int = L.BN_OBJECTIVE_BLUE,
+               user_tag: int = 0) -> int:
+        cfg = L.BnConfig(width, height, n_points, generator_g, n_pairs, n_integrands, sigma,
+                         radius, couples_per_sweep, mode, objective, L.BN_SCHEDULE_AUTO, seed)
+        req = L.BnRequest(cfg, n_sweeps, 0, user_tag)
+        rid = ctypes.c_int64()
+        L.check(L.load().bn_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
+        return rid.value
+
+    def cancel(self, request_id: int) -> None:
+        L.check(L.load().bn_server_cancel(self._h, request_id))
+
+    def poll(self, cap: int = 256) -> list[Result]:
+        buf = (L.BnResult * cap)()
+        n = ctypes.c_int32()
+        L.check(L.load().bn_server_poll(self._h, buf, cap, ctypes.byref(n)))
+        return [Result(r.request_id, r.user_tag, r.status, r.n_pairs, r.width, r.height,
+                       tuple(r.energy[:r.n_pairs]), r.t_submit, r.t_admit, r.t_done)
+                for r in buf[:n.value]]
+
+    def take_shifts(self, result: Result) -> np.ndarray:
+        out = np.empty((result.n_pairs, result.height, result.width, 2), np.float32)
+        L.check(L.load().bn_server_take_shifts(self._h, result.request_id, out.ctypes.data,
+                                               out.size))
+        return out
+
+    def stats(self) -> dict:
+        st = L.BnServerStats()
+        L.check(L.load().bn_server_get_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in L.BnServerStats._fields_}
+
+    def drain(self, timeout_s: float = 600.0) -> None:
+        L.check(L.load().bn_server_drain(self._h, timeout_s))
+
+    def close(self) -> None:
+        if self._h:
+            L.load().bn_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

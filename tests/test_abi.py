@@ -80,3 +80,74 @@ def test_null_arguments(lib):
 def test_selftest_arguments_validated_on_the_host(lib):
     assert lib.bn_selftest_wait_timeout(2, 1 << 20) == L.BN_ERR_INVALID_ARG
     assert lib.bn_selftest_wait_timeout(0, 10) == L.BN_ERR_INVALID_ARG
+
+
+_LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "bn_sampler.h"
+#define S(T) printf(#T " size %zu\n", sizeof(T));
+#define O(T, F) printf(#T " " #F " %zu\n", offsetof(T, F));
+int main(void) {
+    S(bn_config) O(bn_config, sigma) O(bn_config, seed)
+    S(bn_sweep_stats) S(bn_info) O(bn_info, sweep)
+    S(bn_kernel_time) O(bn_kernel_time, launches)
+    S(bn_schedule) O(bn_schedule, tsplit)
+    S(bn_server_config) O(bn_server_config, memory_budget_bytes)
+    S(bn_request) O(bn_request, n_sweeps) O(bn_request, user_tag)
+    S(bn_result) O(bn_result, status) O(bn_result, energy) O(bn_result, t_done)
+    S(bn_server_stats) O(bn_server_stats, memory_budget)
+    return 0;
+}
+"""
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", L.os.path.dirname(L.HEADER), str(src), "-o",
+                    str(exe)], check=True)
+    seen = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        name, field, value = line.split()
+        seen[(name, field)] = int(value)
+    py = {"bn_config": L.BnConfig, "bn_sweep_stats": L.BnSweepStats, "bn_info": L.BnInfo,
+          "bn_kernel_time": L.BnKernelTime, "bn_schedule": L.BnSchedule,
+          "bn_server_config": L.BnServerConfig, "bn_request": L.BnRequest,
+          "bn_result": L.BnResult, "bn_server_stats": L.BnServerStats}
+    for (name, field), value in seen.items():
+        cls = py[name]
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == value, (name, field, got, value)
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(max_slots=0), "max_slots"),
+    (dict(max_slots=5000), "max_slots"),
+    (dict(sweeps_per_chunk=0), "sweeps_per_chunk"),
+    (dict(sweeps_per_chunk=501), "sweeps_per_chunk"),
+    (dict(memory_budget_bytes=-1), "budget"),
+])
+def test_server_config_validated_on_the_host(lib, kw, needle):
+    base = dict(device=0, max_slots=4, sweeps_per_chunk=10, reserved=0, memory_budget_bytes=0)
+    base.update(kw)
+    h = ctypes.c_void_p()
+    assert lib.bn_server_create(ctypes.byref(L.BnServerConfig(**base)),
+                                ctypes.byref(h)) == L.BN_ERR_INVALID_ARG
+    assert needle in lib.bn_last_error().decode()
+    assert not h.value
+
+
+def test_server_null_arguments(lib):
+    h = ctypes.c_void_p()
+    n = ctypes.c_int32()
+    assert lib.bn_server_create(None, ctypes.byref(h)) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_server_submit(None, None, None) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_server_cancel(None, 1) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_server_poll(None, None, 0, ctypes.byref(n)) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_server_take_shifts(None, 1, None, 0) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_server_get_stats(None, None) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_server_drain(None, 0.0) == L.BN_ERR_INVALID_ARG
+    lib.bn_server_destroy(None)

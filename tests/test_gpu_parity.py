@@ -280,6 +280,33 @@ def test_persistent_batch_equals_each_alone(pkg):
         m.close()
 
 
+@pytest.mark.parametrize("kind", ["plain", "persistent"])
+def test_batch_per_member_budgets(pkg, kind):
+    """bn_batch_optimize_each: each member stops at its own pass budget inside the fused launch
+    (zero included), and ends exactly where it would alone; its pass counter says so."""
+    cfgs = [(32, 32, 16, 64, 1), (48, 40, 4, 256, 1), (64, 64, 64, 128, 2), (40, 24, 256, 128, 1)]
+    budgets = [[7, 0, 13, 3], [5, 9, 0, 11]]
+    sched = pkg.BN_SCHEDULE_PLAIN if kind == "plain" else pkg.BN_SCHEDULE_AUTO
+    mixed = [pkg.Sampler(W, H, N, T, seed=W * 3 + H, n_pairs=p, schedule=sched)
+             for W, H, N, T, p in cfgs]
+    b = pkg.Batch(mixed)
+    want = pkg.BN_SCHEDULE_PLAIN if kind == "plain" else pkg.BN_SCHEDULE_PERSISTENT
+    assert b.get_schedule()["kind"] == want
+    total = [0] * len(cfgs)
+    for bud in budgets:
+        b.optimize_each(bud, stats=False)
+        total = [t + x for t, x in zip(total, bud)]
+    for m, (W, H, N, T, p), n in zip(mixed, cfgs, total):
+        assert m.get_state()[0] == n
+        with pkg.Sampler(W, H, N, T, seed=W * 3 + H, n_pairs=p) as a:
+            a.optimize(n, stats=False)
+            assert np.array_equal(m.shifts(), a.shifts())
+            assert np.array_equal(m.energy(), a.energy())
+    b.close()
+    for m in mixed:
+        m.close()
+
+
 def test_autotune_leaves_state_alone_and_keeps_results(pkg):
     cfgs = [(48, 40, 16, 128, 1), (64, 64, 64, 256, 1), (40, 40, 256, 128, 2)]
     tiles = [pkg.Sampler(W, H, N, T, seed=W * 7 + H, n_pairs=p) for W, H, N, T, p in cfgs]

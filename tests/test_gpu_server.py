@@ -1,0 +1,141 @@
+"""Serving loop (continuous batching) on the GPU: every request's outcome equals the same request
+run alone through a Sampler, whatever else is resident, however the passes are chunked and
+whenever it is admitted; admission respects the slot and memory limits; cancellation."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2105_12620_gb300 import BnError, Sampler, Server  # noqa: E402
+from paper_2105_12620_gb300 import _lib as L  # noqa: E402
+
+# (width, height, N, T, n_pairs, passes, seed): non-power-of-two tiles, 8- and 16-bit counts
+MIX_PERSISTENT = [
+    (24, 20, 16, 64, 1, 23, 11),
+    (32, 32, 64, 256, 2, 40, 12),
+    (40, 28, 32, 128, 1, 31, 13),
+    (20, 20, 256, 64, 2, 12, 14),
+    (48, 36, 128, 192, 1, 19, 15),
+    (33, 47, 64, 1024, 1, 9, 16),
+]
+# a 16 x 16 tile is too small for the persistent kernel: batches holding it run plain
+MIX_PLAIN = [
+    (16, 16, 128, 128, 1, 17, 21),
+    (24, 24, 16, 64, 2, 26, 22),
+    (13, 29, 32, 96, 1, 11, 23),
+]
+
+
+def alone(w, h, n, t, pairs, passes, seed):
+    with Sampler(w, h, n, t, seed=seed, n_pairs=pairs) as s:
+        s.optimize(passes, stats=False)
+        return np.asarray(s.energy()), s.shifts()
+
+
+def run_server(mix, max_slots, chunk, late=()):
+    with Server(max_slots=max_slots, sweeps_per_chunk=chunk) as sv:
+        ids = {}
+        for k, (w, h, n, t, pairs, passes, seed) in enumerate(mix):
+            ids[sv.submit(w, h, n, t, passes, seed=seed, n_pairs=pairs, user_tag=k)] = k
+        if late:  # arrive while the first wave is on the GPU
+            t0 = time.time()
+            while sv.stats()["chunks"] < 1 and time.time() - t0 < 60:
+                time.sleep(0.001)
+            for k, (w, h, n, t, pairs, passes, seed) in enumerate(late, start=len(mix)):
+                ids[sv.submit(w, h, n, t, passes, seed=seed, n_pairs=pairs, user_tag=k)] = k
+        sv.drain(300.0)
+        results = sv.poll(1024)
+        out = {}
+        for r in results:
+            assert r.status == L.BN_OK
+            assert ids[r.request_id] == r.user_tag
+            out[r.user_tag] = (np.asarray(r.energy), sv.take_shifts(r), r)
+        stats = sv.stats()
+    return out, stats
+
+
+@pytest.mark.parametrize("mix,max_slots,chunk", [
+    (MIX_PERSISTENT, 3, 7),
+    (MIX_PERSISTENT, 16, 5),
+    (MIX_PLAIN, 2, 6),
+    (MIX_PERSISTENT[:3] + MIX_PLAIN[:2], 4, 9),
+])
+def test_each_result_equals_the_request_alone(mix, max_slots, chunk):
+    out, stats = run_server(mix, max_slots, chunk)
+    assert stats["completed"] == len(mix) and stats["failed"] == 0
+    assert stats["pending"] == 0 and stats["active"] == 0 and stats["memory_in_use"] == 0
+    for k, cfg in enumerate(mix):
+        e_ref, sh_ref = alone(*cfg)
+        e, sh, r = out[k]
+        np.testing.assert_array_equal(sh, sh_ref)
+        np.testing.assert_array_equal(e, e_ref)
+        assert r.t_submit <= r.t_admit <= r.t_done
+
+
+def test_requests_arriving_mid_flight_are_admitted_and_exact():
+    first, late = MIX_PERSISTENT[:3], MIX_PERSISTENT[3:]
+    out, stats = run_server(first, 8, 4, late=late)
+    assert stats["completed"] == len(first) + len(late)
+    for k, cfg in enumerate(first + late):
+        e_ref, sh_ref = alone(*cfg)
+        np.testing.assert_array_equal(out[k][1], sh_ref)
+        np.testing.assert_array_equal(out[k][0], e_ref)
+
+
+def test_proposal_count_matches_the_budgets():
+    mix = MIX_PERSISTENT[:4]
+    _, stats = run_server(mix, 2, 6)
+    expect = 0
+    for (w, h, n, t, pairs, passes, seed) in mix:
+        with Sampler(w, h, n, t, seed=seed, n_pairs=pairs) as s:
+            expect += s.info.couples * pairs * passes
+    assert stats["proposals"] == expect
+
+
+def test_memory_budget_serialises_admission_and_rejects_oversize():
+    cfg = (64, 64, 64, 1024, 1, 30, 31)
+    with Sampler(*cfg[:4], seed=cfg[6]) as s:
+        bytes_one = s.info.device_bytes
+    # room for one such request at a time
+    with Server(max_slots=8, sweeps_per_chunk=10,
+                memory_budget_bytes=int(bytes_one * 1.6) + (1 << 20)) as sv:
+        for k in range(3):
+            sv.submit(*cfg[:4], cfg[5], seed=cfg[6] + k, user_tag=k)
+        with pytest.raises(BnError) as ei:
+            sv.submit(256, 256, 64, 1024, 10)
+        assert ei.value.code == L.BN_ERR_BUSY
+        sv.drain(300.0)
+        res = sorted(sv.poll(16), key=lambda r: r.t_admit)
+        st = sv.stats()
+    assert st["rejected"] == 1 and st["completed"] == 3
+    assert [r.status for r in res] == [L.BN_OK] * 3
+    for a, b in zip(res, res[1:]):
+        assert b.t_admit >= a.t_done  # never two resident at once
+    for r in res:
+        with Sampler(*cfg[:4], seed=cfg[6] + r.user_tag) as s:
+            s.optimize(cfg[5], stats=False)
+            np.testing.assert_array_equal(np.asarray(r.energy), np.asarray(s.energy()))
+
+
+def test_cancel_pending_and_resident():
+    with Server(max_slots=1, sweeps_per_chunk=5) as sv:
+        a = sv.submit(64, 64, 64, 512, 400, seed=1, user_tag=0)
+        b = sv.submit(32, 32, 16, 64, 10, seed=2, user_tag=1)
+        c = sv.submit(32, 32, 16, 64, 10, seed=3, user_tag=2)
+        sv.cancel(b)
+        t0 = time.time()
+        while sv.stats()["chunks"] < 2 and time.time() - t0 < 60:
+            time.sleep(0.001)
+        sv.cancel(a)
+        sv.drain(120.0)
+        res = {r.request_id: r for r in sv.poll(16)}
+        st = sv.stats()
+        assert res[a].status == L.BN_ERR_BAD_STATE and res[b].status == L.BN_ERR_BAD_STATE
+        assert res[c].status == L.BN_OK
+        assert st["cancelled"] == 2 and st["completed"] == 1 and st["memory_in_use"] == 0
+        with pytest.raises(BnError):
+            sv.cancel(12345)
