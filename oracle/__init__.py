@@ -212,7 +212,7 @@ class OracleTile:
         self.objective = objective
         self.mode = mode
         self.g = generator_g if generator_g else pick_g(n_points)
-        self.M = couples_per_sweep if couples_per_sweep else (1 << self.L) // 8
+        self.M = couples_per_sweep if couples_per_sweep else max(1, (1 << self.L) // 8)
         self.U = shifts(seed, pair, self.P)
         self.a, self.b, self.C = heaviside_bank(seed, pair, n_integrands)
         self.perm = permutation(seed, pair, self.L)

@@ -38,6 +38,8 @@ CONFIGS = [
     (4, 4, 2, 7, 1, 6, 9),            # tiny torus: every other pixel is a neighbour
     (9, 6, 32, 33, 1, 3, 4),          # other radius, non-square
     (64, 32, 128, 130, 1, 6, 11),     # N = 128 (16-bit), ragged T
+    (2, 2, 8, 5, 1, 6, 1),            # smallest torus: one couple per pass, every swap a tie
+    (3, 2, 16, 9, 1, 2, 6),           # P = 6 < 8 padded to 8: invalid couples occur
 ]
 
 
