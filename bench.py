@@ -57,6 +57,33 @@ def proposals_per_tile(sweeps: int = SWEEPS) -> int:
     return sweeps * P // 8  # P is a power of two: every couple of every pass is valid
 
 
+def all_reduce_list(values, dist, device: str, op: str = "max") -> list[float]:
+    """Reduce a few host numbers over all ranks (max for times: the slowest rank bounds the job;
+    sum for work done)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
+def merge_serving(summary: dict, dist, device: str) -> dict:
+    """Whole-job serving figures: worst rank's latencies and makespan, summed work."""
+    if dist is None:
+        return summary
+    keys = ("p50_latency_s", "p99_latency_s", "p99_queue_s", "makespan_s")
+    out = dict(summary)
+    for k, v in zip(keys, all_reduce_list([summary[k] for k in keys], dist, device, "max")):
+        out[k] = v
+    props, done = all_reduce_list([summary["proposals_per_s"] * summary["makespan_s"],
+                                   summary["completed"]], dist, device, "sum")
+    out["proposals_per_s"] = props / out["makespan_s"]
+    out["served_req_per_s"] = done / out["makespan_s"]
+    out["completed"] = int(done)
+    return out
+
+
 def parse_clocks(text: str, gpu_index: int | None = None) -> dict:
     rows = []
     for line in text.strip().splitlines():
@@ -200,8 +227,6 @@ def plain_per_tile(pkg, stream, rank, sweeps: int = 500, reps: int = 3) -> dict:
 def run_serving(pkg, args, rank: int, local: int, world: int, dist) -> dict:
     """Bounded run of the serving loop: a Poisson stream of mixed requests per GPU (weak
     scaling: every rank serves its own stream); latencies are the worst rank's."""
-    import torch
-
     from paper_2105_12620_gb300 import serving as srv
 
     reqs = srv.draw_requests(args.serving_requests, args.serving_rate, seed=1000 + rank)
@@ -209,17 +234,7 @@ def run_serving(pkg, args, rank: int, local: int, world: int, dist) -> dict:
                     device=local) as sv:
         summary = srv.run_load(sv, reqs, timeout_s=args.serving_timeout)
         summary["server"] = sv.stats()
-    if dist is not None:
-        keys = ("p50_latency_s", "p99_latency_s", "makespan_s")
-        t = torch.tensor([summary[k] for k in keys], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        for k, v in zip(keys, t.tolist()):
-            summary[k] = v
-        tot = torch.tensor([summary["proposals_per_s"] * summary["makespan_s"],
-                            summary["completed"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tot)
-        summary["proposals_per_s"] = float(tot[0]) / summary["makespan_s"]
-        summary["served_req_per_s"] = float(tot[1]) / summary["makespan_s"]
+    summary = merge_serving(summary, dist, "cuda")
     summary["config"] = {
         "stream": f"Poisson {args.serving_rate:g} req/s per GPU, {args.serving_requests} "
                   "requests (bounded run), side log-uniform 32..512, N in {16,64,256}, T=1024, "
@@ -332,10 +347,7 @@ def run_ours(args) -> int:
         del host_energy
     total_ms = local_ms
     e2e_total = sum(e2e_ms)
-    if dist is not None:
-        tt = torch.tensor([local_ms, e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, e2e_total = float(tt[0]), float(tt[1])
+    total_ms, e2e_total = all_reduce_list([local_ms, e2e_total], dist, "cuda", "max")
     props_step = B * proposals_per_tile(args.sweeps)
     value = world * props_step * args.steps / (total_ms / 1000.0)
     e2e_value = world * props_step * args.steps / (e2e_total / 1000.0)

@@ -43,10 +43,10 @@ def draw_requests(n: int, rate_hz: float = 200.0, seed: int = 0, side=(32, 512),
 
 
 def couples_per_pass(width: int, height: int) -> int:
-    """Couples proposed per pass with the default setting: 2^ceil(log2 P) / 8."""
+    """Couples proposed per pass with the default setting: 2^ceil(log2 P) / 8, at least one."""
     P = width * height
-    L = max(1, (P - 1).bit_length())
-    return (1 << L) // 8
+    L = (P - 1).bit_length()
+    return max(1, (1 << L) // 8)
 
 
 def offered_proposals(reqs: list[Request]) -> int:
