@@ -246,3 +246,29 @@ class OracleTile:
                                     couples)
         self.sweep_index += 1
         return SweepLog(dE, S, flags, couples, committed)
+
+
+# ---------------------------------------------------------------------------------------------
+# renderer-side lookup (Sec. 3.1 padding, Sec. 3.2 sampler): samples for a window of screen
+# pixels, tile repeated over the screen, dimensions taken in pairs
+# ---------------------------------------------------------------------------------------------
+def screen_samples(N: int, g: int, U_pairs, W: int, H: int, x0: int, y0: int, width: int,
+                   height: int, first: int, count: int, n_dims: int) -> np.ndarray:
+    """float64 [height][width][count][n_dims]: sample k = first + j of screen pixel
+    (x0 + i, y0 + r) in dimension d is coordinate d % 2 of mod(s^k + u_p, 1) for the tile of
+    dimension pair d // 2, with p the tile pixel (x mod W, y mod H).  U_pairs[i] holds the
+    shift now at each pixel of pair i ([P, 2] uint32).  An odd n_dims drops the second
+    coordinate of the last pair (it is padding)."""
+    out = np.zeros((height, width, count, n_dims), np.float64)
+    for r in range(height):
+        for i in range(width):
+            p = ((y0 + r) % H) * W + ((x0 + i) % W)
+            for pair in range((n_dims + 1) // 2):
+                U = U_pairs[pair]
+                x, y = points(N, g, U[p, 0] / 4294967296.0, U[p, 1] / 4294967296.0)
+                for j in range(count):
+                    k = first + j
+                    out[r, i, j, 2 * pair] = x[k]
+                    if 2 * pair + 1 < n_dims:
+                        out[r, i, j, 2 * pair + 1] = y[k]
+    return out

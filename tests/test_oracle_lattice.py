@@ -97,3 +97,29 @@ def test_unshifted_lattice_is_a_group():
     for p in pts:
         for q in pts:
             assert ((p[0] - q[0]) % N, (p[1] - q[1]) % N) in pts
+
+
+def test_screen_samples_wrap_pairs_and_padding():
+    """Renderer lookup: the tile repeats over the screen, dimensions come in pairs, each pair
+    from its own tile, and an odd dimension count drops the padding coordinate."""
+    W, H, N = 5, 3, 16
+    g = oracle.pick_g(N)
+    U = [oracle.shifts(2, 0, W * H), oracle.shifts(2, 1, W * H)]
+    s = oracle.screen_samples(N, g, U, W, H, -7, 4, 12, 5, 3, 9, 3)
+    assert s.shape == (5, 12, 9, 3)
+    # screen pixel (x, y) and (x + W, y - H) read the same tile pixel
+    assert np.array_equal(s[:, :7], s[:, 5:12])
+    assert np.array_equal(s[0], oracle.screen_samples(N, g, U, W, H, -7, 4 + H, 12, 1, 3, 9, 3)[0])
+    # each pair's N samples of a pixel are its shifted lattice: every 1-D projection is the
+    # N-point grid j / N shifted by the pixel's u (mod 1)
+    full = oracle.screen_samples(N, g, U, W, H, 0, 0, W, H, 0, N, 4)
+    for p in range(W * H):
+        y, x = divmod(p, W)
+        for pair in range(2):
+            for c in range(2):
+                u = U[pair][p, c] / 2**32
+                v = np.sort((full[y, x, :, 2 * pair + c] - u) % 1.0)
+                assert np.allclose(v, np.arange(N) / N, atol=1e-12)
+    # the odd dimension count keeps the first coordinate of the last pair only
+    assert np.array_equal(s[..., 2], oracle.screen_samples(N, g, U, W, H, -7, 4, 12, 5, 3, 9,
+                                                           4)[..., 2])
