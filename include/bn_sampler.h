@@ -216,6 +216,41 @@ int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out);
  * Synchronises. */
 int bn_sampler_autotune(bn_sampler *s, int32_t trial_sweeps, bn_schedule *chosen);
 
+/* ---- evaluation of a tile (Sec. 3.3, Sec. 3.5) ------------------------------------------------
+ * Criterion of Fig. 1c: for each integrand the error tile (estimate minus exact integral) is
+ * filtered by a Gaussian of standard deviation sigma (pixels) and the RMSE over integrands and
+ * pixels is returned per sigma: rmse = sqrt(mean_t mean_p ((k_sigma * e_t)(p))^2).
+ * The filter is the sampled Gaussian exp(-d^2 / (2 sigma^2)) wrapped around the toroidal tile
+ * and normalised to sum 1, applied along x then y; sigma <= 0 leaves the error unfiltered.
+ *   integrands  BN_INTEGRANDS_HEAVISIDE: the first n_integrands Heavisides of the pair's bank
+ *               (estimate k_p[t] / N, reference the exact area within the unit square);
+ *               BN_INTEGRANDS_GAUSSIAN: n_integrands (<= 4096) smooth bumps
+ *               exp(-|x - c|^2 / (2 s^2)), c uniform in [0,1)^2 and s uniform in [0.05, 0.5)
+ *               from Philox tag 7 (estimate: mean over the pixel's N shifted lattice points;
+ *               reference: closed form with erf).  The Sec. 3.5 check: the optimiser never
+ *               sees these, yet their filtered error drops too.
+ *   sigmas      host, n_sigma (1..64) floats; rmse_out: host, n_sigma doubles.
+ * FP64 throughout.  Uses temporary device memory (stream-ordered); synchronises. */
+#define BN_INTEGRANDS_HEAVISIDE 0
+#define BN_INTEGRANDS_GAUSSIAN 1
+int bn_evaluate_criterion(bn_sampler *s, int32_t pair, int32_t integrands, int32_t n_integrands,
+                          const float *sigmas, int32_t n_sigma, double *rmse_out);
+
+/* ---- renderer lookup (Sec. 3.1, Sec. 3.2) ---------------------------------------------------
+ * bn_export_shift_table writes the pair's current per-pixel shifts (uint32 [height][width][2],
+ * 0.32 fixed point) to device memory (enqueued only), for the device function bn_sample() of
+ * include/bn_sample.cuh that a renderer's kernels call.
+ * bn_generate_samples fills out[r][i][j][d] = sample first_sample + j of screen pixel
+ * (x0 + i, y0 + r) in dimension d: the tile repeats over the screen (negative coordinates
+ * wrap too), dimension d reads coordinate d % 2 of pair d / 2, so n_dims <= 2 n_pairs; an odd
+ * n_dims leaves out the second coordinate of the last pair (the padding of Sec. 3.1).  Values
+ * are multiples of 2^-24 in [0, 1).  first_sample + n_samples <= n_points.  out: device when
+ * out_is_device, else host (then the call synchronises). */
+int bn_export_shift_table(bn_sampler *s, int32_t pair, uint32_t *out_device, size_t n_words);
+int bn_generate_samples(bn_sampler *s, int32_t x0, int32_t y0, int32_t width, int32_t height,
+                        int32_t first_sample, int32_t n_samples, int32_t n_dims, float *out,
+                        size_t n_floats, int32_t out_is_device);
+
 /* ---- batches: many samplers swept together in one launch sequence ------------------------- */
 typedef struct bn_batch bn_batch;
 

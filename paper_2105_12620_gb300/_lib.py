@@ -20,6 +20,7 @@ BN_ERR_INVALID_ARG, BN_ERR_OOM, BN_ERR_CUDA, BN_ERR_TIMEOUT, BN_ERR_BUSY, BN_ERR
 BN_MODE_NONINTERACTING, BN_MODE_CONCURRENT = 0, 1
 BN_OBJECTIVE_BLUE, BN_OBJECTIVE_LITERAL = -1, 1
 BN_SCHEDULE_AUTO, BN_SCHEDULE_PLAIN, BN_SCHEDULE_PERSISTENT = 0, 1, 2
+BN_INTEGRANDS_HEAVISIDE, BN_INTEGRANDS_GAUSSIAN = 0, 1
 
 
 class BnConfig(ctypes.Structure):
@@ -127,6 +128,12 @@ _SIGS = {
     "bn_evaluate_energy_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.c_float, ctypes.c_int32, _P, _P]),
+    "bn_evaluate_criterion": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             _P, ctypes.c_int32, _P]),
+    "bn_export_shift_table": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
+    "bn_generate_samples": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, _P, ctypes.c_size_t, ctypes.c_int32]),
     "bn_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P,
                                        ctypes.POINTER(_P)]),
     "bn_batch_optimize": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSweepStats)]),

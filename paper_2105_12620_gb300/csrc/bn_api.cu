@@ -687,6 +687,85 @@ int bn_fetch_points(bn_sampler *s, int32_t pair, int32_t pixel, float *out, size
     return BN_OK;
 }
 
+int bn_evaluate_criterion(bn_sampler *s, int32_t pair, int32_t integrands, int32_t n_integrands,
+                          const float *sigmas, int32_t n_sigma, double *rmse_out)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (!sigmas || !rmse_out) return fail(BN_ERR_INVALID_ARG, "null sigmas or output");
+    if (integrands != BN_INTEGRANDS_HEAVISIDE && integrands != BN_INTEGRANDS_GAUSSIAN)
+        return fail(BN_ERR_INVALID_ARG, "integrands must be BN_INTEGRANDS_HEAVISIDE or _GAUSSIAN");
+    const int most = integrands == BN_INTEGRANDS_HEAVISIDE ? h.T : 4096;
+    if (n_integrands < 1 || n_integrands > most)
+        return fail(BN_ERR_INVALID_ARG, "n_integrands must be in [1, %d]", most);
+    if (n_sigma < 1 || n_sigma > 64) return fail(BN_ERR_INVALID_ARG, "n_sigma must be in [1, 64]");
+    for (int i = 0; i < n_sigma; ++i)
+        if (!std::isfinite(sigmas[i]) || sigmas[i] > 4096.f)
+            return fail(BN_ERR_INVALID_ARG, "sigma must be finite and at most 4096");
+    if (int rc = set_device(s)) return rc;
+    std::vector<double> sums(n_sigma, 0.0);
+    BN_CUDA(bn::criterion_sums(s->dprob + pair, h, integrands, n_integrands, sigmas, n_sigma,
+                               sums.data(), s->stream));
+    if (int rc = check_device_error(s)) return rc;
+    const double cells = (double)h.P * (double)n_integrands;
+    for (int i = 0; i < n_sigma; ++i) rmse_out[i] = std::sqrt(sums[i] / cells);
+    return BN_OK;
+}
+
+int bn_export_shift_table(bn_sampler *s, int32_t pair, uint32_t *out_device, size_t n_words)
+{
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (!out_device || n_words < (size_t)2 * h.P)
+        return fail(BN_ERR_INVALID_ARG, "output buffer must hold 2 * width * height words");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(bn::launch_shift_table(s->dprob + pair, h, out_device, s->stream));
+    return BN_OK;
+}
+
+int bn_generate_samples(bn_sampler *s, int32_t x0, int32_t y0, int32_t width, int32_t height,
+                        int32_t first_sample, int32_t n_samples, int32_t n_dims, float *out,
+                        size_t n_floats, int32_t out_is_device)
+{
+    if (!s || !out) return fail(BN_ERR_INVALID_ARG, "null argument");
+    const bn::Problem &h = s->hprob[0];
+    if (width < 1 || height < 1 || n_samples < 1 || first_sample < 0 ||
+        (long long)first_sample + n_samples > h.N)
+        return fail(BN_ERR_INVALID_ARG, "need width, height, n_samples >= 1 and "
+                    "0 <= first_sample, first_sample + n_samples <= n_points (%d)", h.N);
+    if (n_dims < 1 || n_dims > 2 * s->n_prob)
+        return fail(BN_ERR_INVALID_ARG, "n_dims must be in [1, 2 * n_pairs] (%d)", 2 * s->n_prob);
+    const long long need = (long long)width * height * n_samples * n_dims;
+    if (need > (1ll << 31)) return fail(BN_ERR_INVALID_ARG, "more than 2^31 values requested");
+    if (n_floats < (size_t)need) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
+    if (int rc = set_device(s)) return rc;
+    bn_sample_table tb;
+    memset(&tb, 0, sizeof tb);
+    tb.width = h.W;
+    tb.height = h.H;
+    tb.n_pairs = s->n_prob;
+    tb.log2_points = h.m;
+    tb.generator_g = h.g;
+    uint32_t *tables = nullptr;
+    float *dout = out_is_device ? out : nullptr;
+    BN_CUDA(cudaMallocAsync(&tables, sizeof(uint32_t) * 2 * h.P * s->n_prob, s->stream));
+    if (!out_is_device) BN_CUDA(cudaMallocAsync(&dout, sizeof(float) * need, s->stream));
+    for (int i = 0; i < s->n_prob; ++i) {
+        BN_CUDA(bn::launch_shift_table(s->dprob + i, h, tables + (size_t)2 * h.P * i, s->stream));
+        tb.shifts[i] = tables + (size_t)2 * h.P * i;
+    }
+    BN_CUDA(bn::launch_samples(tb, x0, y0, width, height, first_sample, n_samples, n_dims, dout,
+                               s->stream));
+    if (!out_is_device) {
+        BN_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * need, cudaMemcpyDeviceToHost,
+                                s->stream));
+        BN_CUDA(cudaFreeAsync(dout, s->stream));
+    }
+    BN_CUDA(cudaFreeAsync(tables, s->stream));
+    if (!out_is_device) BN_CUDA(cudaStreamSynchronize(s->stream));
+    return BN_OK;
+}
+
 int bn_fetch_counts(bn_sampler *s, int32_t pair, int32_t *out, size_t n)
 {
     if (int rc = check_pair(s, pair)) return rc;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "bn_device.cuh"
+#include "bn_sample.cuh"
 #include "bn_sampler.h"
 
 namespace bn {
@@ -30,6 +31,14 @@ cudaError_t launch_fetch_points(const Problem *dprob, const Problem &h, int pixe
                                 cudaStream_t st);
 cudaError_t launch_unpack_counts(const Problem *dprob, const Problem &h, int32_t *out,
                                  cudaStream_t st);
+
+// evaluation criterion and renderer lookup (bn_criterion.cu)
+cudaError_t criterion_sums(const Problem *dprob, const Problem &h, int kind, int n_int,
+                           const float *sigmas, int n_sigma, double *sums, cudaStream_t st);
+cudaError_t launch_shift_table(const Problem *dprob, const Problem &h, uint32_t *out,
+                               cudaStream_t st);
+cudaError_t launch_samples(const bn_sample_table &tb, int x0, int y0, int width, int height,
+                           int first, int count, int n_dims, float *out, cudaStream_t st);
 
 // energy, Eq. 1 (bn_energy.cu)
 cudaError_t launch_energy(const Problem *dprob, const Problem *hprob, int n_prob,

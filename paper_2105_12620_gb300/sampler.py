@@ -133,6 +133,35 @@ class Sampler:
         L.check(L.load().bn_fetch_shifts(self._h, out.ctypes.data, out.size, 0))
         return out
 
+    def criterion(self, sigmas, integrands: str = "heaviside", n_integrands: int | None = None,
+                  pair: int = 0) -> np.ndarray:
+        """Filtered-error RMSE per sigma (Sec. 3.3) for the Heaviside bank or smooth bumps."""
+        sig = np.ascontiguousarray(sigmas, np.float32).ravel()
+        kind = {"heaviside": L.BN_INTEGRANDS_HEAVISIDE, "gaussian": L.BN_INTEGRANDS_GAUSSIAN}[
+            integrands]
+        n = n_integrands if n_integrands else (self.n_integrands if kind == 0 else 256)
+        out = np.zeros(sig.size, np.float64)
+        L.check(L.load().bn_evaluate_criterion(self._h, pair, kind, n, sig.ctypes.data, sig.size,
+                                               out.ctypes.data))
+        return out
+
+    def shift_table_into(self, pair: int, device_ptr: int, n_words: int) -> None:
+        """Current per-pixel shifts (uint32 [H][W][2]) into device memory, for bn_sample()."""
+        L.check(L.load().bn_export_shift_table(self._h, pair, device_ptr, n_words))
+
+    def samples(self, x0: int, y0: int, width: int, height: int, first: int, count: int,
+                n_dims: int) -> np.ndarray:
+        """Renderer lookup: float32 [height][width][count][n_dims] for a window of the screen."""
+        out = np.zeros((height, width, count, n_dims), np.float32)
+        L.check(L.load().bn_generate_samples(self._h, x0, y0, width, height, first, count, n_dims,
+                                             out.ctypes.data, out.size, 0))
+        return out
+
+    def samples_into(self, device_ptr: int, n_floats: int, x0: int, y0: int, width: int,
+                     height: int, first: int, count: int, n_dims: int) -> None:
+        L.check(L.load().bn_generate_samples(self._h, x0, y0, width, height, first, count, n_dims,
+                                             device_ptr, n_floats, 1))
+
     def shifts_into(self, device_ptr: int, n_floats: int) -> None:
         L.check(L.load().bn_fetch_shifts(self._h, device_ptr, n_floats, 1))
 

@@ -151,3 +151,9 @@ def test_server_null_arguments(lib):
     assert lib.bn_server_get_stats(None, None) == L.BN_ERR_INVALID_ARG
     assert lib.bn_server_drain(None, 0.0) == L.BN_ERR_INVALID_ARG
     lib.bn_server_destroy(None)
+
+
+def test_criterion_and_lookup_null_arguments(lib):
+    assert lib.bn_evaluate_criterion(None, 0, 0, 1, None, 1, None) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_export_shift_table(None, 0, None, 0) == L.BN_ERR_INVALID_ARG
+    assert lib.bn_generate_samples(None, 0, 0, 1, 1, 0, 1, 1, None, 0, 0) == L.BN_ERR_INVALID_ARG
