@@ -208,6 +208,12 @@ typedef struct bn_schedule {
 int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc);
 int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out);
 
+/* Plain schedule: sweeps run as replays of a CUDA graph that holds passes_per_graph passes
+ * (three kernels each), captured on first use; 0 launches every kernel directly.  Default 32.
+ * Results are identical either way; per-kernel timing (bn_set_kernel_timing) bypasses the
+ * graphs.  Synchronises the stream and drops graphs already captured. */
+int bn_sampler_set_graph_passes(bn_sampler *s, int32_t passes_per_graph);
+
 /* Autotuner: time every instantiated schedule (CTA shape x chunk split, plain as fallback) for
  * trial_sweeps passes on a scratch copy of the device state, keep the fastest, and cache the
  * choice per workload signature (tile sizes, N, T, couples, radius, SM count) in the process and,
@@ -267,6 +273,7 @@ int bn_batch_optimize_each(bn_batch *b, const int32_t *n_sweeps_per_member,
 int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc);
 int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen);
 int bn_batch_get_schedule(bn_batch *b, bn_schedule *out);
+int bn_batch_set_graph_passes(bn_batch *b, int32_t passes_per_graph);
 void bn_batch_destroy(bn_batch *b);
 
 /* ---- serving: continuous batching of sampler-generation requests --------------------------

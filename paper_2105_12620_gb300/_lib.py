@@ -123,6 +123,8 @@ _SIGS = {
     "bn_sampler_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
     "bn_batch_set_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
     "bn_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(BnSchedule)]),
+    "bn_sampler_set_graph_passes": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "bn_batch_set_graph_passes": (ctypes.c_int, [_P, ctypes.c_int32]),
     "bn_sampler_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSchedule)]),
     "bn_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BnSchedule)]),
     "bn_evaluate_energy_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32,

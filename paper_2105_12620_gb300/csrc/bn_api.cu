@@ -111,7 +111,19 @@ struct SweepPlan {
     bn::GridBarrier *d_bar = nullptr;
     int *d_work = nullptr;          // [2] phase-1 unit counters
     int n_prob = 0, max_M = 0, sms = 0;
+    // plain schedule: passes per captured CUDA graph (0 = launch every kernel directly); the
+    // graphs hold the problem pointers, so they live and die with the plan
+    int graph_passes = 32;
+    cudaStream_t capture = nullptr;     // captures cannot run on the legacy default stream
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
+
+void free_graphs(SweepPlan &pl)
+{
+    for (auto &g : pl.graph)
+        if (g) cudaGraphExecDestroy(g);
+    pl.graph[0] = pl.graph[1] = nullptr;
+}
 
 void free_plan(SweepPlan &pl)
 {
@@ -121,6 +133,9 @@ void free_plan(SweepPlan &pl)
     pl.d_prefix = nullptr;
     pl.d_bar = nullptr;
     pl.d_work = nullptr;
+    free_graphs(pl);
+    if (pl.capture) cudaStreamDestroy(pl.capture);
+    pl.capture = nullptr;
 }
 
 }  // namespace
@@ -422,15 +437,48 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
 
 constexpr int kItersPerLaunch = 500;
 
-int run_plan(const SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Problem> &hp,
+// Capture graph_passes passes of the plain schedule (three launches each) as one CUDA graph.
+// Every kernel reads the pass index and budget from device memory, so the graph replays.
+int capture_plain(SweepPlan &pl, const bn::SweepLaunch &sl, int g)
+{
+    if (!pl.capture) BN_CUDA(cudaStreamCreateWithFlags(&pl.capture, cudaStreamNonBlocking));
+    BN_CUDA(cudaStreamBeginCapture(pl.capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < pl.graph_passes && e == cudaSuccess; ++k)
+        e = bn::launch_plain_sweep(sl, pl.capture, nullptr);
+    bn::note_launches(-3ll * pl.graph_passes);  // captured, not launched
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(pl.capture, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&pl.graph[g], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        pl.graph[g] = nullptr;
+        return fail(BN_ERR_CUDA, "capture of the plain sweep graph failed: %s",
+                    cudaGetErrorString(e));
+    }
+    return BN_OK;
+}
+
+int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Problem> &hp,
              int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm, bool set_end = true)
 {
     if (set_end) BN_CUDA(bn::launch_set_end(dprob, pl.n_prob, n_sweeps, 1, st));
     if (!pl.persistent) {
+        // per-kernel timing needs the individual launches
+        const bool graphs = pl.graph_passes > 0 && !(tm && tm->enabled);
         for (int g = 0; g < 2; ++g) {
             if (!pl.count[g]) continue;
             bn::SweepLaunch sl{dprob + pl.first[g], pl.count[g], pl.max_M, g + 1};
-            for (int32_t k = 0; k < n_sweeps; ++k) BN_CUDA(bn::launch_plain_sweep(sl, st, tm));
+            int32_t k = 0;
+            if (graphs && n_sweeps >= pl.graph_passes) {
+                if (!pl.graph[g])
+                    if (int rc = capture_plain(pl, sl, g)) return rc;
+                for (; k + pl.graph_passes <= n_sweeps; k += pl.graph_passes)
+                    BN_CUDA(cudaGraphLaunch(pl.graph[g], st));
+                bn::note_launches(3ll * pl.graph_passes * ((n_sweeps / pl.graph_passes)));
+            }
+            for (; k < n_sweeps; ++k) BN_CUDA(bn::launch_plain_sweep(sl, st, tm));
         }
         return BN_OK;
     }
@@ -1207,6 +1255,27 @@ int bn_batch_autotune(bn_batch *b, int32_t trial_sweeps, bn_schedule *chosen)
 {
     if (!b) return fail(BN_ERR_INVALID_ARG, "null batch");
     return autotune_entry(b->members, b->all, b->dprob, b->stream, trial_sweeps, b->plan, chosen);
+}
+
+int bn_sampler_set_graph_passes(bn_sampler *s, int32_t passes)
+{
+    if (!s || passes < 0 || passes > 4096)
+        return fail(BN_ERR_INVALID_ARG, "passes per graph must be in [0, 4096]");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    free_graphs(s->plan);
+    s->plan.graph_passes = passes;
+    return BN_OK;
+}
+
+int bn_batch_set_graph_passes(bn_batch *b, int32_t passes)
+{
+    if (!b || passes < 0 || passes > 4096)
+        return fail(BN_ERR_INVALID_ARG, "passes per graph must be in [0, 4096]");
+    BN_CUDA(cudaStreamSynchronize(b->stream));
+    free_graphs(b->plan);
+    b->plan.graph_passes = passes;
+    return BN_OK;
 }
 
 int bn_batch_get_schedule(bn_batch *b, bn_schedule *out)

@@ -105,6 +105,10 @@ class Sampler:
         sc = _schedule(kind, shape, tsplit)
         L.check(L.load().bn_sampler_set_schedule(self._h, ctypes.byref(sc)))
 
+    def set_graph_passes(self, passes: int) -> None:
+        """Plain schedule: passes per captured CUDA graph (0 = direct launches)."""
+        L.check(L.load().bn_sampler_set_graph_passes(self._h, passes))
+
     def get_schedule(self) -> dict:
         sc = L.BnSchedule()
         L.check(L.load().bn_sampler_get_schedule(self._h, ctypes.byref(sc)))
@@ -238,6 +242,9 @@ class Batch:
     def set_schedule(self, kind: int, shape=None, tsplit: int = 0) -> None:
         sc = _schedule(kind, shape, tsplit)
         L.check(L.load().bn_batch_set_schedule(self._h, ctypes.byref(sc)))
+
+    def set_graph_passes(self, passes: int) -> None:
+        L.check(L.load().bn_batch_set_graph_passes(self._h, passes))
 
     def get_schedule(self) -> dict:
         sc = L.BnSchedule()

@@ -309,6 +309,44 @@ def test_batch_per_member_budgets(pkg, kind):
         m.close()
 
 
+def test_plain_graphs_do_not_change_results(pkg):
+    """Plain schedule replayed from captured CUDA graphs (several graph sizes, pass counts that
+    are not multiples of them) equals direct launches, alone and in a batch."""
+    def run(graph, cfg, passes):
+        W, H, N, T, pairs, seed = cfg
+        s = pkg.Sampler(W, H, N, T, seed=seed, n_pairs=pairs, schedule=pkg.BN_SCHEDULE_PLAIN)
+        s.set_graph_passes(graph)
+        for n in passes:
+            s.optimize(n, stats=False)
+        out = (s.shifts(), s.sweep_log(0), s.energy(), s.get_state()[0])
+        s.close()
+        return out
+
+    for cfg in [(32, 32, 16, 64, 1, 3), (45, 37, 128, 100, 2, 4), (9, 6, 8, 20, 1, 5)]:
+        base = run(0, cfg, [75, 40])
+        for graph in (1, 7, 32):
+            got = run(graph, cfg, [75, 40])
+            assert np.array_equal(got[0], base[0]) and np.array_equal(got[2], base[2])
+            assert got[3] == base[3] == 115
+            for x, y in zip(got[1], base[1]):
+                assert np.array_equal(x, y)
+    cfgs = [(32, 32, 16, 64, 1), (20, 36, 4, 256, 1), (10, 10, 64, 32, 2)]
+    tiles = [pkg.Sampler(W, H, N, T, seed=W + H, n_pairs=p, schedule=pkg.BN_SCHEDULE_PLAIN)
+             for W, H, N, T, p in cfgs]
+    b = pkg.Batch(tiles)
+    b.set_graph_passes(8)
+    b.optimize(37, stats=False)
+    b.optimize_each([20, 0, 9], stats=False)
+    for t, (W, H, N, T, p), n in zip(tiles, cfgs, (57, 37, 46)):
+        with pkg.Sampler(W, H, N, T, seed=W + H, n_pairs=p, schedule=pkg.BN_SCHEDULE_PLAIN) as a:
+            a.set_graph_passes(0)
+            a.optimize(n, stats=False)
+            assert np.array_equal(t.shifts(), a.shifts())
+    b.close()
+    for t in tiles:
+        t.close()
+
+
 def test_autotune_leaves_state_alone_and_keeps_results(pkg):
     cfgs = [(48, 40, 16, 128, 1), (64, 64, 64, 256, 1), (40, 40, 256, 128, 2)]
     tiles = [pkg.Sampler(W, H, N, T, seed=W * 7 + H, n_pairs=p) for W, H, N, T, p in cfgs]
