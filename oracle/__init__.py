@@ -150,6 +150,21 @@ def counts(N: int, g: int, U: np.ndarray, a, b, C) -> np.ndarray:
     return k
 
 
+def _counts_part(args):
+    return counts(*args)
+
+
+def counts_parallel(N: int, g: int, U: np.ndarray, a, b, C, workers: int) -> np.ndarray:
+    """counts() over pixel ranges in a pool of spawned processes (same arithmetic per pixel;
+    spawned, so that it is safe in a process that already uses a GPU)."""
+    import multiprocessing as mp
+    P = U.shape[0]
+    step = max(1, -(-P // (4 * workers)))
+    parts = [(N, g, U[i:i + step], a, b, C) for i in range(0, P, step)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return np.concatenate(pool.map(_counts_part, parts), axis=0)
+
+
 def torus_d2(W: int, H: int, p: int, q: int) -> int:
     return lib().bno_torus_d2(W, H, p, q)
 
@@ -203,7 +218,7 @@ class OracleTile:
 
     def __init__(self, width, height, n_points, n_integrands, seed, pair=0, generator_g=0,
                  sigma=2.1, radius=6, couples_per_sweep=0, objective=OBJECTIVE_BLUE,
-                 mode=MODE_NONINTERACTING):
+                 mode=MODE_NONINTERACTING, workers=1):
         self.W, self.H, self.N, self.T = width, height, n_points, n_integrands
         self.P = width * height
         self.L = log2_ceil(self.P)
@@ -216,7 +231,10 @@ class OracleTile:
         self.U = shifts(seed, pair, self.P)
         self.a, self.b, self.C = heaviside_bank(seed, pair, n_integrands)
         self.perm = permutation(seed, pair, self.L)
-        self.k = counts(self.N, self.g, self.U, self.a, self.b, self.C)
+        if workers > 1:
+            self.k = counts_parallel(self.N, self.g, self.U, self.a, self.b, self.C, workers)
+        else:
+            self.k = counts(self.N, self.g, self.U, self.a, self.b, self.C)
         self.sidx = np.arange(self.P, dtype=np.int32)
         self.sweep_index = 0
 

@@ -133,3 +133,20 @@ def test_rank_reductions_world_size_two_gloo():
         assert merged["proposals_per_s"] == pytest.approx(1.5e6)
         assert merged["completed"] == 11
         assert merged["served_req_per_s"] == pytest.approx(11 / 20.0)
+
+
+def test_workload_definitions():
+    from paper_2105_12620_gb300 import workloads as wl
+    c4 = wl.c4()
+    assert len(c4) == 96 and c4 == wl.c4()
+    assert {t.width for t in c4} == {32, 64, 128, 256}
+    assert {t.n_points for t in c4} == {4, 16, 64} and {t.n_integrands for t in c4} == {256, 1024}
+    assert all(t.width == t.height and t.sweeps == 2000 and t.n_pairs == 1 for t in c4)
+    c3 = wl.c3()[0]
+    assert (c3.width, c3.n_points, c3.n_integrands, c3.n_pairs, c3.sweeps) == (256, 256, 512, 2,
+                                                                               4000)
+    assert c3.couples() == 8192 and wl.c2()[0].couples() == 2048 and wl.c1()[0].couples() == 128
+    assert wl.c2()[0].proposals() == 2048 * 2000
+    # every workload is a valid configuration: 24 T N^2 < 2^31
+    for t in c4 + [c3] + wl.c2() + wl.c1():
+        assert 24 * t.n_integrands * t.n_points ** 2 < 2 ** 31

@@ -102,3 +102,11 @@ def test_shifts_are_24_bit_uniform():
     n = len(u)
     assert np.max(np.abs(u - (np.arange(1, n + 1) - 0.5) / n)) < 1.8 / math.sqrt(n)
     assert not np.array_equal(oracle.shifts(7, 0, 64), oracle.shifts(7, 1, 64))
+
+
+def test_parallel_counts_equal_serial_counts():
+    N, g = 16, oracle.pick_g(16)
+    U = oracle.shifts(3, 0, 37)
+    a, b, C = oracle.heaviside_bank(3, 0, 21)
+    assert np.array_equal(oracle.counts_parallel(N, g, U, a, b, C, 3),
+                          oracle.counts(N, g, U, a, b, C))
