@@ -38,6 +38,8 @@ STENCIL_OFFSETS = 112           # neighbours within radius 6 on a tile >= 13 x 1
 L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
 # nominal int8 dot-product (IDP4A) peak: 152 SMs x 64 IDP4A/clk x 4 MAC x 2.07 GHz
 DP4A_PEAK_TOPS = 152 * 64 * 4 * 2.07e9 / 1e12
+# 16-bit counts: one multiply-accumulate per IMAD, 64 IMAD/clk/SM
+IMAD_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -248,6 +250,27 @@ def run_serving(pkg, args, rank: int, local: int, world: int, dist) -> dict:
     return summary
 
 
+def workload_tiles(args):
+    """(tiles, description) of the benchmarked workload; sweeps override the pass budget."""
+    from paper_2105_12620_gb300 import workloads as wl
+    if args.workload == "c2":
+        tiles = wl.c2(args.tiles)
+        desc = WORKLOAD
+    elif args.workload == "c3":
+        tiles = wl.c3()
+        desc = ("256x256 toroidal tile, two pairs of dimensions, rank-1 lattice N=256 (g=71), "
+                "T=512 Heavisides per pair (int16 counts), Eq.1 sigma 2.1 radius 6, 4000 passes")
+    else:
+        tiles = wl.c4()
+        desc = ("96 tiles, side in {32,64,128,256}, N in {4,16,64}, T in {256,1024} (Philox "
+                "seed 0), Eq.1 sigma 2.1 radius 6, 2000 passes, fused in one batch")
+    if args.sweeps:
+        desc = desc.replace(f"{tiles[0].sweeps} passes", f"{args.sweeps} passes")
+        tiles = [wl.Tile(t.width, t.height, t.n_points, t.n_integrands, t.n_pairs, args.sweeps)
+                 for t in tiles]
+    return tiles, desc
+
+
 def run_ours(args) -> int:
     import torch
 
@@ -272,12 +295,15 @@ def run_ours(args) -> int:
     from paper_2105_12620_gb300 import _lib as L
 
     stream = torch.cuda.Stream()
-    B = args.tiles
+    specs, desc = workload_tiles(args)
+    B = len(specs)
+    sweeps = specs[0].sweeps  # every tile of a workload has the same pass budget
     schedule = {"auto": pkg.BN_SCHEDULE_AUTO, "plain": pkg.BN_SCHEDULE_PLAIN,
                 "persistent": pkg.BN_SCHEDULE_PERSISTENT}[args.schedule]
-    tiles = [pkg.Sampler(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=tile_seed(rank, 0, i, B),
-                         sigma=SIGMA, radius=RADIUS, schedule=schedule, stream=stream)
-             for i in range(B)]
+    tiles = [pkg.Sampler(t.width, t.height, t.n_points, t.n_integrands,
+                         seed=tile_seed(rank, 0, i, B), n_pairs=t.n_pairs, sigma=SIGMA,
+                         radius=RADIUS, schedule=schedule, stream=stream)
+             for i, t in enumerate(specs)]
     batch = pkg.Batch(tiles, stream=stream) if B > 1 else None
     chosen = None
     if args.block:
@@ -290,20 +316,30 @@ def run_ours(args) -> int:
     elif args.schedule == "auto":
         # untimed: trial passes on a scratch copy pick the CTA shape / chunk split
         chosen = batch.autotune(20) if batch is not None else tiles[0].autotune(20)
-    shifts_dev = torch.empty((B, H_TILE, W_TILE, 2), dtype=torch.float32, device="cuda")
-    energy_dev = torch.empty((B,), dtype=torch.float64, device="cuda")
+    shift_floats = [t.width * t.height * 2 * t.n_pairs for t in specs]
+    shifts_dev = torch.empty(sum(shift_floats), dtype=torch.float32, device="cuda")
+    shift_off = [0]
+    for n in shift_floats:
+        shift_off.append(shift_off[-1] + n)
+    energy_dev = torch.empty(sum(t.n_pairs for t in specs), dtype=torch.float64, device="cuda")
+    energy_off = [0]
+    for t in specs:
+        energy_off.append(energy_off[-1] + t.n_pairs)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def optimize_all():
+        if batch is not None:
+            batch.optimize(sweeps, stats=False)
+        else:
+            tiles[0].optimize(sweeps, stats=False)
 
     def step(k: int):
         for i, t in enumerate(tiles):
             t.reset(tile_seed(rank, k, i, B))
-        if batch is not None:
-            batch.optimize(args.sweeps, stats=False)
-        else:
-            tiles[0].optimize(args.sweeps, stats=False)
+        optimize_all()
         for i, t in enumerate(tiles):
-            t.energy_into(energy_dev[i:i + 1].data_ptr())
-            t.shifts_into(shifts_dev[i].data_ptr(), shifts_dev[i].numel())
+            t.energy_into(energy_dev[energy_off[i]:energy_off[i + 1]].data_ptr())
+            t.shifts_into(shifts_dev[shift_off[i]:].data_ptr(), shift_floats[i])
 
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
@@ -334,51 +370,47 @@ def run_ours(args) -> int:
         local_ms = sum(step_ms)
         # end to end through the public API with host buffers (pinned staging inside)
         e2e_ms = []
-        host_shifts = None
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for i, t in enumerate(tiles):
                 t.reset(tile_seed(rank, 10_000 + k, i, B))
-            if batch is not None:
-                batch.optimize(args.sweeps, stats=False)
-            else:
-                tiles[0].optimize(args.sweeps, stats=False)
+            optimize_all()
             host_shifts = [t.shifts() for t in tiles]
             host_energy = [t.energy() for t in tiles]
             e2e_ms.append(1000 * (time.perf_counter() - t0))
-        del host_energy
-    total_ms = local_ms
-    e2e_total = sum(e2e_ms)
-    total_ms, e2e_total = all_reduce_list([local_ms, e2e_total], dist, "cuda", "max")
-    props_step = B * proposals_per_tile(args.sweeps)
+        del host_energy, host_shifts
+    total_ms, e2e_total = all_reduce_list([local_ms, sum(e2e_ms)], dist, "cuda", "max")
+    props_step = sum(t.proposals() for t in specs)
     value = world * props_step * args.steps / (total_ms / 1000.0)
     e2e_value = world * props_step * args.steps / (e2e_total / 1000.0)
 
-    # dominant kernel and its roofline
+    # dominant kernel and its roofline: algorithmic multiply-accumulates of the couples' swap
+    # terms, 2 sides x 112 neighbours x T per proposal, over that kernel's measured time
     dom = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
     roofline = None
     if dom:
         name, (nl, tms) = dom
-        per_prop_ops = 2 * STENCIL_OFFSETS * T_INTEGRANDS
-        # algorithmic int8 multiply-accumulates over the timed region / that kernel's time
-        total_ops = B * args.steps * proposals_per_tile(args.sweeps) * per_prop_ops
+        total_ops = args.steps * sum(t.proposals() * 2 * STENCIL_OFFSETS * t.n_integrands
+                                     for t in specs)
+        wide = any(t.n_points > 64 for t in specs)
+        peak = IMAD_PEAK_TOPS if wide else DP4A_PEAK_TOPS
         achieved = total_ops / (tms / 1000.0) / 1e12
-        roofline = {"kernel": name, "bound": "alu", "achieved": achieved,
-                    "peak": DP4A_PEAK_TOPS, "unit": "TOP/s", "frac": achieved / DP4A_PEAK_TOPS,
-                    "traffic": None,
-                    "note": "op = one int8 multiply-accumulate; peak = IDP4A nominal "
-                            "(152 SMs x 64/clk x 4 x 2.07 GHz)",
+        roofline = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
+                    "note": ("op = one int16 multiply-accumulate; peak = IMAD nominal "
+                             "(152 SMs x 64/clk x 2.07 GHz)") if wide else
+                            ("op = one int8 multiply-accumulate; peak = IDP4A nominal "
+                             "(152 SMs x 64/clk x 4 x 2.07 GHz)"),
                     "launches": nl, "avg_launch_ms": tms / nl,
                     "share": tms / max(sum(v[1] for v in ktimes.values()), 1e-9)}
     plain = None
-    if not args.no_plain and rank == 0:
+    if not args.no_plain and rank == 0 and args.workload == "c2":
         plain = plain_per_tile(pkg, stream, rank)
     serving = None
-    if args.serving_requests > 0:
+    if args.serving_requests > 0 and args.workload == "c2":
         serving = run_serving(pkg, args, rank, local, world, dist)
-    line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -389,8 +421,9 @@ def run_ours(args) -> int:
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tiles_per_gpu": B, "sweeps": args.sweeps,
+            "dtype": "int16" if any(t.n_points > 64 for t in specs) else "int8",
+            "data": "synthetic",
+            "config": {"workload": desc, "tiles_per_gpu": B, "sweeps": sweeps,
                        "schedule": args.schedule if chosen is None else
                        {"kind": "persistent" if chosen["kind"] == pkg.BN_SCHEDULE_PERSISTENT
                         else "plain", "block": chosen["shape"][:2],
@@ -400,8 +433,8 @@ def run_ours(args) -> int:
                        "l2": "flushed between steps (256 MB write)"},
             "tiles_per_s": world * B * args.steps / (total_ms / 1000.0),
             "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": B * int(tiles[0].info.reset_h2d_bytes),
-                    "d2h_bytes_per_step": B * (W_TILE * H_TILE * 2 * 4 + 8)},
+                    "h2d_bytes_per_step": sum(int(t.info.reset_h2d_bytes) for t in tiles),
+                    "d2h_bytes_per_step": sum(4 * n for n in shift_floats) + 8 * energy_off[-1]},
             "gpu_launches": int(launches),
             "clocks": {k: clock_info[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "roofline": roofline,
@@ -421,14 +454,62 @@ def run_ours(args) -> int:
     return 0
 
 
+def report_modes(args) -> int:
+    """Eq. 1 and the filtered error along the passes for the two commit rules on one 128 x 128
+    tile: keep only non-interacting improving couples, or every improving couple (the paper's
+    GPU optimiser, which may move Eq. 1 the wrong way at first)."""
+    import paper_2105_12620_gb300 as pkg
+    from paper_2105_12620_gb300 import build as pkg_build
+    pkg_build.build()
+    pkg.load()
+    every, total = 100, args.sweeps or SWEEPS
+    out = {"report": "commit rule", "workload": WORKLOAD.rsplit(",", 1)[0],
+           "every": every, "passes": total, "sigmas": [1.0, 2.0, 4.0, 8.0]}
+    for name, mode in (("noninteracting", pkg.BN_MODE_NONINTERACTING),
+                       ("concurrent", pkg.BN_MODE_CONCURRENT)):
+        s = pkg.Sampler(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=1, sigma=SIGMA,
+                        radius=RADIUS, mode=mode)
+        trace, worse = [float(s.energy()[0])], 0
+        committed = 0
+        for _ in range(total // every):
+            st = s.optimize(every)
+            committed += st.committed
+            trace.append(float(s.energy()[0]))
+        # passes whose own commits lowered Eq. 1 (objective: raise it)
+        s2 = pkg.Sampler(W_TILE, H_TILE, N_POINTS, T_INTEGRANDS, seed=1, sigma=SIGMA,
+                         radius=RADIUS, mode=mode)
+        prev = float(s2.energy()[0])
+        for _ in range(200):
+            s2.optimize(1, stats=False)
+            e = float(s2.energy()[0])
+            worse += e < prev
+            prev = e
+        s2.close()
+        out[name] = {"energy": trace, "committed": int(committed),
+                     "passes_that_lowered_eq1_of_first_200": int(worse),
+                     "rmse_initial_vs_final": None}
+        crit = s.criterion(out["sigmas"])
+        s.reset(1)
+        out[name]["rmse_initial_vs_final"] = [list(map(float, s.criterion(out["sigmas"]))),
+                                              list(map(float, crit))]
+        s.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--tiles", type=int, default=32, help="tiles per GPU per step")
-    ap.add_argument("--sweeps", type=int, default=SWEEPS)
+    ap.add_argument("--tiles", type=int, default=32, help="128x128 tiles per GPU per step")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4"], default="c2",
+                    help="c2: 128x128 N=64 T=1024 tiles (default); c3: 256x256 N=256, two "
+                         "pairs x T=512; c4: 96 mixed tiles")
+    ap.add_argument("--sweeps", type=int, default=0, help="pass budget (0: the workload's)")
+    ap.add_argument("--report", choices=["modes"], default=None,
+                    help="modes: Eq. 1 along the passes for both commit rules (no timing)")
     ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto")
     ap.add_argument("--cpu-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -446,6 +527,8 @@ def main(argv=None) -> int:
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.report == "modes":
+        return report_modes(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
