@@ -44,6 +44,13 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+# DRAM bytes (read + write) per tile-pass of the persistent sweep kernel, 8x8 CTA shape, int8
+# counts, working set larger than L2: one ncu capture of 16 tiles x 6 passes (the profile summary
+# of k_persistent for 128x128 N=64 T=1024); a launch's traffic scales with its tile-passes
+TRAFFIC_PER_TILE_PASS = (1683.924e6 + 58.356e6) / (16 * 6)
+PASSES_PER_LAUNCH = 500
+# shared-memory wavefront rate: 128 B per SM clock, measured 120 B/clk/SM by a probe
+SMEM_PEAK_TBS = 152 * 120 * 2.07e9 / 1e12
 
 
 # ------------------------------------------------------------------------------------------------
@@ -397,8 +404,20 @@ def run_ours(args) -> int:
         wide = any(t.n_points > 64 for t in specs)
         peak = IMAD_PEAK_TOPS if wide else DP4A_PEAK_TOPS
         achieved = total_ops / (tms / 1000.0) / 1e12
+        traffic = None
+        sched = chosen or {}
+        if (args.workload == "c2" and not wide and sched.get("kind") == pkg.BN_SCHEDULE_PERSISTENT
+                and tuple(sched.get("shape", ())[:2]) == (8, 8)):
+            traffic = TRAFFIC_PER_TILE_PASS * B * min(sweeps, PASSES_PER_LAUNCH)
         roofline = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "TOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TOP/s", "frac": achieved / peak, "traffic": traffic,
+                    "traffic_note": "DRAM bytes per launch, scaled by tile-passes from an ncu "
+                                    "capture of 16 tiles x 6 passes" if traffic else None,
+                    "smem": {"achieved": achieved, "peak": SMEM_PEAK_TBS, "unit": "TB/s",
+                             "frac": achieved / SMEM_PEAK_TBS,
+                             "note": "the stencil reads one shared-memory byte per "
+                                     "multiply-accumulate; peak = probed wavefront rate"}
+                    if not wide else None,
                     "note": ("op = one int16 multiply-accumulate; peak = IMAD nominal "
                              "(152 SMs x 64/clk x 2.07 GHz)") if wide else
                             ("op = one int8 multiply-accumulate; peak = IDP4A nominal "
