@@ -522,7 +522,7 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--tiles", type=int, default=32, help="128x128 tiles per GPU per step")
+    ap.add_argument("--tiles", type=int, default=64, help="128x128 tiles per GPU per step")
     ap.add_argument("--workload", choices=["c2", "c3", "c4"], default="c2",
                     help="c2: 128x128 N=64 T=1024 tiles (default); c3: 256x256 N=256, two "
                          "pairs x T=512; c4: 96 mixed tiles")
