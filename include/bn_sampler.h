@@ -196,8 +196,11 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
 /* ---- execution schedule (speed only; results do not depend on it) ------------------------ */
 /* kind: BN_SCHEDULE_*.  For the persistent kernel, block_x x block_y pixels per work unit,
  * threads per CTA and proposed pixels per compute warp per round must name an instantiated
- * shape (16x8/512/4, 8x16/512/4, 8x8/256/4); tsplit = chunk ranges per block (1..4, 0 = auto).
- * block_x = 0 keeps the default shape.  set synchronises the stream. */
+ * shape (8x8/256/4, 16x8/512/4, 8x16/512/4, 8x8/512/4; a shape that does not fit the
+ * tiles gives way to the first one that does); tsplit = chunk ranges per block
+ * (1..4, 0 = auto).  8x8/512/4 evaluates 8-bit counts on the tensor cores (mma.sync f16, exact
+ * for N <= 64) and needs tile sides that are multiples of 8, at least 24.  block_x = 0 keeps the
+ * default shape.  set synchronises the stream. */
 typedef struct bn_schedule {
     int32_t kind;
     int32_t block_x, block_y;

@@ -86,8 +86,10 @@ class BnServerStats(ctypes.Structure):
         "active", "chunks", "proposals", "memory_in_use", "memory_budget")]
 
 
-# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, pixels/warp)
-PERSISTENT_SHAPES = [(8, 8, 256, 4), (16, 8, 512, 4), (8, 16, 512, 4)]
+# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, pixels/warp);
+# (8, 8, 512, 4) is the tensor-core variant for 8-bit counts on tiles of width 8k >= 24
+PERSISTENT_SHAPES = [(8, 8, 256, 4), (16, 8, 512, 4), (8, 16, 512, 4), (8, 8, 512, 4)]
+MMA_SHAPE = (8, 8, 512, 4)
 
 
 class BnError(RuntimeError):

@@ -110,6 +110,7 @@ struct SweepPlan {
     int *d_prefix = nullptr;        // [2][2][n_prob + 1] unit / couple prefix sums
     bn::GridBarrier *d_bar = nullptr;
     int *d_work = nullptr;          // [2] phase-1 unit counters
+    char *d_tmaps = nullptr;        // [n_prob] TMA tensor maps (tensor-core shape only)
     int n_prob = 0, max_M = 0, sms = 0;
     // plain schedule: passes per captured CUDA graph (0 = launch every kernel directly); the
     // graphs hold the problem pointers, so they live and die with the plan
@@ -130,9 +131,11 @@ void free_plan(SweepPlan &pl)
     if (pl.d_prefix) cudaFree(pl.d_prefix);
     if (pl.d_bar) cudaFree(pl.d_bar);
     if (pl.d_work) cudaFree(pl.d_work);
+    if (pl.d_tmaps) cudaFree(pl.d_tmaps);
     pl.d_prefix = nullptr;
     pl.d_bar = nullptr;
     pl.d_work = nullptr;
+    pl.d_tmaps = nullptr;
     free_graphs(pl);
     if (pl.capture) cudaStreamDestroy(pl.capture);
     pl.capture = nullptr;
@@ -431,6 +434,16 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
     BN_CUDA(cudaMemcpy(pl.d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     BN_CUDA(cudaMalloc(&pl.d_bar, sizeof(bn::GridBarrier)));
     BN_CUDA(cudaMalloc(&pl.d_work, 2 * sizeof(int)));
+    if (bn::persistent_shape_is_mma(pl.shape) && pl.count[0] > 0) {
+        // tensor maps of the 8-bit problems' count planes, in problem order
+        const size_t per = (size_t)bn::kTensorMapsPerProblem * bn::kTensorMapBytes;
+        std::vector<char> maps((size_t)pl.n_prob * per, 0);
+        for (int i = 0; i < pl.n_prob; ++i)
+            if (hp[i].count_bytes == 1)
+                BN_CUDA(bn::encode_count_tensor_maps(hp[i], maps.data() + (size_t)i * per));
+        BN_CUDA(cudaMalloc(&pl.d_tmaps, maps.size()));
+        BN_CUDA(cudaMemcpy(pl.d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
+    }
     (void)dprob;
     return BN_OK;
 }
@@ -494,6 +507,9 @@ int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Prob
         a.tsplit = pl.shape.tsplit;
         a.bar = pl.d_bar;
         a.work = pl.d_work;
+        a.tmaps = pl.d_tmaps ? pl.d_tmaps + (size_t)pl.first[g] * bn::kTensorMapsPerProblem *
+                                                bn::kTensorMapBytes
+                             : nullptr;
         for (int32_t done = 0; done < n_sweeps; done += kItersPerLaunch) {
             a.n_iter = n_sweeps - done < kItersPerLaunch ? n_sweeps - done : kItersPerLaunch;
             BN_CUDA(cudaMemsetAsync(pl.d_bar, 0, sizeof(bn::GridBarrier), st));
