@@ -316,6 +316,25 @@ int64_t bn::estimate_device_bytes(const bn_config &c)
 
 namespace {
 
+// Stream-ordered scratch, released on every return path
+struct StreamScratch {
+    void *ptr = nullptr;
+    cudaStream_t st = nullptr;
+    explicit StreamScratch(cudaStream_t s) : st(s) {}
+    StreamScratch(const StreamScratch &) = delete;
+    StreamScratch &operator=(const StreamScratch &) = delete;
+    ~StreamScratch()
+    {
+        if (ptr) cudaFreeAsync(ptr, st);
+    }
+    cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&ptr, bytes, st); }
+    template <typename T>
+    T *as() const
+    {
+        return static_cast<T *>(ptr);
+    }
+};
+
 int check_pair(bn_sampler *s, int32_t pair)
 {
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
@@ -566,11 +585,11 @@ int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
     if (e == cudaSuccess) e = cudaMalloc(&s->d_shifts, sizeof(float) * shift_floats);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_shifts, sizeof(float) * shift_floats);
     if (e != cudaSuccess) {
+        const size_t bytes = s->slab_bytes;
         bn_sampler_destroy(s);
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? BN_ERR_OOM : BN_ERR_CUDA,
-                    "device allocation of %zu bytes failed: %s", s->slab_bytes,
-                    cudaGetErrorString(e));
+                    "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     Slab real;
     real.base = s->slab;
@@ -741,12 +760,11 @@ int bn_fetch_points(bn_sampler *s, int32_t pair, int32_t pixel, float *out, size
     if (!out || pixel < 0 || pixel >= h.P || n_floats < (size_t)2 * h.N)
         return fail(BN_ERR_INVALID_ARG, "bad pixel or buffer");
     if (int rc = set_device(s)) return rc;
-    float *tmp = nullptr;
-    BN_CUDA(cudaMallocAsync(&tmp, sizeof(float) * 2 * h.N, s->stream));
-    BN_CUDA(bn::launch_fetch_points(s->dprob + pair, h, pixel, tmp, s->stream));
-    BN_CUDA(cudaMemcpyAsync(out, tmp, sizeof(float) * 2 * h.N, cudaMemcpyDeviceToHost,
+    StreamScratch tmp(s->stream);
+    BN_CUDA(tmp.alloc(sizeof(float) * 2 * h.N));
+    BN_CUDA(bn::launch_fetch_points(s->dprob + pair, h, pixel, tmp.as<float>(), s->stream));
+    BN_CUDA(cudaMemcpyAsync(out, tmp.ptr, sizeof(float) * 2 * h.N, cudaMemcpyDeviceToHost,
                             s->stream));
-    BN_CUDA(cudaFreeAsync(tmp, s->stream));
     BN_CUDA(cudaStreamSynchronize(s->stream));
     return BN_OK;
 }
@@ -810,10 +828,11 @@ int bn_generate_samples(bn_sampler *s, int32_t x0, int32_t y0, int32_t width, in
     tb.n_pairs = s->n_prob;
     tb.log2_points = h.m;
     tb.generator_g = h.g;
-    uint32_t *tables = nullptr;
-    float *dout = out_is_device ? out : nullptr;
-    BN_CUDA(cudaMallocAsync(&tables, sizeof(uint32_t) * 2 * h.P * s->n_prob, s->stream));
-    if (!out_is_device) BN_CUDA(cudaMallocAsync(&dout, sizeof(float) * need, s->stream));
+    StreamScratch table_buf(s->stream), out_buf(s->stream);
+    BN_CUDA(table_buf.alloc(sizeof(uint32_t) * 2 * h.P * s->n_prob));
+    if (!out_is_device) BN_CUDA(out_buf.alloc(sizeof(float) * need));
+    uint32_t *tables = table_buf.as<uint32_t>();
+    float *dout = out_is_device ? out : out_buf.as<float>();
     for (int i = 0; i < s->n_prob; ++i) {
         BN_CUDA(bn::launch_shift_table(s->dprob + i, h, tables + (size_t)2 * h.P * i, s->stream));
         tb.shifts[i] = tables + (size_t)2 * h.P * i;
@@ -823,10 +842,8 @@ int bn_generate_samples(bn_sampler *s, int32_t x0, int32_t y0, int32_t width, in
     if (!out_is_device) {
         BN_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * need, cudaMemcpyDeviceToHost,
                                 s->stream));
-        BN_CUDA(cudaFreeAsync(dout, s->stream));
+        BN_CUDA(cudaStreamSynchronize(s->stream));
     }
-    BN_CUDA(cudaFreeAsync(tables, s->stream));
-    if (!out_is_device) BN_CUDA(cudaStreamSynchronize(s->stream));
     return BN_OK;
 }
 
@@ -837,12 +854,11 @@ int bn_fetch_counts(bn_sampler *s, int32_t pair, int32_t *out, size_t n)
     const size_t need = (size_t)h.P * h.T;
     if (!out || n < need) return fail(BN_ERR_INVALID_ARG, "output buffer too small");
     if (int rc = set_device(s)) return rc;
-    int32_t *tmp = nullptr;
-    BN_CUDA(cudaMallocAsync(&tmp, sizeof(int32_t) * need, s->stream));
-    BN_CUDA(bn::launch_unpack_counts(s->dprob + pair, h, tmp, s->stream));
-    BN_CUDA(cudaMemcpyAsync(out, tmp, sizeof(int32_t) * need, cudaMemcpyDeviceToHost,
+    StreamScratch tmp(s->stream);
+    BN_CUDA(tmp.alloc(sizeof(int32_t) * need));
+    BN_CUDA(bn::launch_unpack_counts(s->dprob + pair, h, tmp.as<int32_t>(), s->stream));
+    BN_CUDA(cudaMemcpyAsync(out, tmp.ptr, sizeof(int32_t) * need, cudaMemcpyDeviceToHost,
                             s->stream));
-    BN_CUDA(cudaFreeAsync(tmp, s->stream));
     BN_CUDA(cudaStreamSynchronize(s->stream));
     return BN_OK;
 }

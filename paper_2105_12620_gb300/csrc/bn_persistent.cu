@@ -6,24 +6,25 @@
 //     BX x BY pixels of one problem and a range of 128-byte chunks of the count vectors.  The
 //     CTA finds the block's proposed pixels (pixels of a valid couple of this pass).  One
 //     producer warp then streams, chunk by chunk, the block's window (the block plus a halo of
-//     the weight radius, wrapped on the torus) and each proposed pixel's partner chunk into a
-//     two-stage shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion on
-//     an mbarrier); the counts are stored chunk-major, so every window row is one or two
-//     contiguous runs.  The producer runs one unit ahead: it publishes the next unit's proposed
-//     pixels while the compute warps still work on the current one.  The compute warps read
-//     their proposed pixels' partner chunks straight from L2 (prefetched one chunk ahead) and
-//     accumulate, per proposed pixel p and class c,
+//     the weight radius, wrapped on the torus) into a two-stage shared-memory ring with bulk
+//     asynchronous copies (cp.async.bulk, completion on an mbarrier); the counts are stored
+//     chunk-major, so every window row is one or two contiguous runs.  The producer runs one
+//     unit ahead: it publishes the next unit's proposed pixels while the compute warps still
+//     work on the current one.  The compute warps read their proposed pixels' partner chunks
+//     straight from L2 (prefetched one chunk ahead) and accumulate, per proposed pixel p and
+//     class c,
 //         A_c(p) += delta_p . k_q  over q in S_c(p),   delta_p = k_partner - k_p,
 //     with the 112 stencil offsets as compile-time shared-memory displacements (one IDP4A per
 //     four 8-bit counts).  The partner's own term is removed and the 18 class sums are reduced
-//     across the warp by a transposing butterfly and stored.
+//     across the warp by a transposing butterfly and stored.  (A tensor-core variant of this
+//     phase, selected by its own CTA shape, is described further down.)
 //   phase 2 (finalize): one thread per couple adds the 2 x tsplit partial class sums, computes
 //     dL in fp32 (compensated), flags and logs it and, if the swap improves the objective,
-//     claims the couple's pixels in the owner grid.
-//   phase 3 (resolve + commit): one warp per couple: an improving couple is kept unless an
-//     interacting improving couple (a pixel within the radius) has a higher priority; kept
-//     swaps move the count vectors and the shift index.  Owner claims of the previous pass are
-//     cleared here.
+//     claims the couple's pixels in the owner grid; it also clears the couple's claims of the
+//     previous pass.
+//   phase 3 (resolve + commit): improving couples only, one warp each: a couple is kept unless
+//     an interacting improving couple (a pixel within the radius) has a higher priority; kept
+//     swaps move the count vectors and the shift index.
 // Data written inside the launch is read back through L2 (.cg loads) because L1 is not coherent
 // across SMs.  Every wait (grid barrier, mbarrier) has a clock budget; when it runs out the
 // kernel records an error, lets its own copies land (again bounded) and returns.
@@ -328,7 +329,7 @@ struct Pipe {
 };
 
 // Producer warp: takes units from the counter, publishes each unit's proposed pixels, then
-// streams the unit's window chunks (and the proposed pixels' partner chunks) into the ring.
+// streams the unit's window chunks into the ring.
 template <int BX, int BY, int NCW, int SPW>
 __device__ void produce_pass(const PersistentArgs &args, int it, char *smem, Pipe &pp,
                              volatile int *s_abort)
