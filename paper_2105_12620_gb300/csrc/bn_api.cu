@@ -13,6 +13,7 @@
 
 #include "bn_launch.h"
 #include "bn_persistent.h"
+#include "bn_trace.h"
 #include "bn_sampler.h"
 
 namespace {
@@ -558,6 +559,7 @@ const char *bn_last_error(void) { return g_error.c_str(); }
 
 int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
 {
+    bn::TraceRange trace_("bn.sampler_init");
     if (!cfg || !out) return fail(BN_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     int rc = validate(*cfg);
@@ -650,6 +652,7 @@ int bn_get_info(bn_sampler *s, bn_info *info)
 
 int bn_evaluate_energy(bn_sampler *s, double *energy_per_pair)
 {
+    bn::TraceRange trace_("bn.evaluate_energy");
     if (!s || !energy_per_pair) return fail(BN_ERR_INVALID_ARG, "null argument");
     if (int rc = set_device(s)) return rc;
     BN_CUDA(bn::launch_energy(s->dprob, s->hprob.data(), s->n_prob, s->stream));
@@ -725,6 +728,7 @@ extern "C" {
 
 int bn_optimize_sweeps(bn_sampler *s, int32_t n_sweeps, bn_sweep_stats *stats)
 {
+    bn::TraceRange trace_("bn.optimize_sweeps");
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
     if (n_sweeps < 0) return fail(BN_ERR_INVALID_ARG, "n_sweeps must be >= 0");
     if (int rc = set_device(s)) return rc;
@@ -772,6 +776,7 @@ int bn_fetch_points(bn_sampler *s, int32_t pair, int32_t pixel, float *out, size
 int bn_evaluate_criterion(bn_sampler *s, int32_t pair, int32_t integrands, int32_t n_integrands,
                           const float *sigmas, int32_t n_sigma, double *rmse_out)
 {
+    bn::TraceRange trace_("bn.evaluate_criterion");
     if (int rc = check_pair(s, pair)) return rc;
     const bn::Problem &h = s->hprob[pair];
     if (!sigmas || !rmse_out) return fail(BN_ERR_INVALID_ARG, "null sigmas or output");
@@ -952,6 +957,7 @@ int bn_set_state(bn_sampler *s, int64_t sweep, const int32_t *shift_index, size_
 
 int bn_sampler_reset(bn_sampler *s, uint64_t seed)
 {
+    bn::TraceRange trace_("bn.sampler_reset");
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
     if (int rc = set_device(s)) return rc;
     s->cfg.seed = seed;
@@ -1262,6 +1268,7 @@ int bn_batch_set_schedule(bn_batch *b, const bn_schedule *sc)
 int bn_batch_optimize_each(bn_batch *b, const int32_t *n_sweeps_per_member,
                            bn_sweep_stats *stats)
 {
+    bn::TraceRange trace_("bn.batch_optimize_each");
     if (!b || !n_sweeps_per_member) return fail(BN_ERR_INVALID_ARG, "null argument");
     int32_t most = 0;
     for (size_t i = 0; i < b->members.size(); ++i) {
@@ -1320,6 +1327,7 @@ int bn_batch_get_schedule(bn_batch *b, bn_schedule *out)
 // ---- batches ---------------------------------------------------------------------------------
 int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out)
 {
+    bn::TraceRange trace_("bn.batch_create");
     if (!samplers || n <= 0 || !out) return fail(BN_ERR_INVALID_ARG, "bad batch arguments");
     *out = nullptr;
     auto *b = new bn_batch();
@@ -1367,6 +1375,7 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
 
 int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats)
 {
+    bn::TraceRange trace_("bn.batch_optimize");
     if (!b || n_sweeps < 0) return fail(BN_ERR_INVALID_ARG, "bad batch call");
     // order the batch after every member's pending work
     for (auto *m : b->members) {

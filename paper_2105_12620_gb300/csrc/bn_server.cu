@@ -26,6 +26,7 @@
 
 #include "bn_launch.h"
 #include "bn_sampler.h"
+#include "bn_trace.h"
 
 namespace {
 
@@ -137,6 +138,7 @@ void loop(bn_server *sv)
             sv->st.pending = (int64_t)sv->pending.size();
         }
         for (const auto &p : admit) {
+            bn::TraceRange trace_("bn.server.admit");
             Resident r{p.id, p.req, nullptr, p.req.n_sweeps, p.t_submit, 0.0,
                        bn::estimate_device_bytes(p.req.cfg), false};
             const int rc = bn_sampler_init(&p.req.cfg, sv->init, &r.s);
@@ -196,6 +198,7 @@ void loop(bn_server *sv)
             bn_get_info(sv->active[i].s, &info);
             props += (int64_t)n[i] * info.couples * sv->active[i].req.cfg.n_pairs;
         }
+        bn::TraceRange trace_chunk("bn.server.chunk");
         if (bn_batch_optimize_each(sv->batch, n.data(), nullptr) != BN_OK ||
             cudaStreamSynchronize(sv->run) != cudaSuccess) {
             std::lock_guard<std::mutex> lk(sv->mu);
