@@ -237,19 +237,22 @@ def plain_per_tile(pkg, stream, rank, sweeps: int = 512, reps: int = 3) -> dict:
                     "value: CUDA graphs of 32 passes, direct_launches: one launch per kernel"}
 
 
-def run_serving(pkg, args, rank: int, local: int, world: int, dist) -> dict:
+def run_serving(pkg, args, rank: int, local: int, world: int, dist, n_requests: int | None = None,
+                rate: float | None = None) -> dict:
     """Bounded run of the serving loop: a Poisson stream of mixed requests per GPU (weak
     scaling: every rank serves its own stream); latencies are the worst rank's."""
     from paper_2105_12620_gb300 import serving as srv
 
-    reqs = srv.draw_requests(args.serving_requests, args.serving_rate, seed=1000 + rank)
+    n_requests = args.serving_requests if n_requests is None else n_requests
+    rate = args.serving_rate if rate is None else rate
+    reqs = srv.draw_requests(n_requests, rate, seed=1000 + rank)
     with pkg.Server(max_slots=args.serving_slots, sweeps_per_chunk=args.serving_chunk,
                     device=local) as sv:
         summary = srv.run_load(sv, reqs, timeout_s=args.serving_timeout)
         summary["server"] = sv.stats()
     summary = merge_serving(summary, dist, "cuda")
     summary["config"] = {
-        "stream": f"Poisson {args.serving_rate:g} req/s per GPU, {args.serving_requests} "
+        "stream": f"Poisson {rate:g} req/s per GPU, {n_requests} "
                   "requests (bounded run), side log-uniform 32..512, N in {16,64,256}, T=1024, "
                   "1 or 2 pairs, pass budget uniform 500..5000",
         "max_slots": args.serving_slots, "sweeps_per_chunk": args.serving_chunk,
@@ -427,9 +430,13 @@ def run_ours(args) -> int:
     plain = None
     if not args.no_plain and rank == 0 and args.workload == "c2":
         plain = plain_per_tile(pkg, stream, rank)
-    serving = None
+    serving = serving_light = None
     if args.serving_requests > 0 and args.workload == "c2":
         serving = run_serving(pkg, args, rank, local, world, dist)
+        if args.serving_light_requests > 0:
+            # a stream the GPU keeps up with: latencies are service times, not queueing
+            serving_light = run_serving(pkg, args, rank, local, world, dist,
+                                        args.serving_light_requests, args.serving_light_rate)
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -461,6 +468,7 @@ def run_ours(args) -> int:
             "cpu_baseline": cpu,
             "plain_per_tile": plain,
             "serving": serving,
+            "serving_light": serving_light,
         }
         print(json.dumps(line), flush=True)
     if batch is not None:
@@ -543,6 +551,9 @@ def main(argv=None) -> int:
     ap.add_argument("--serving-slots", type=int, default=64)
     ap.add_argument("--serving-chunk", type=int, default=50)
     ap.add_argument("--serving-timeout", type=float, default=300.0)
+    ap.add_argument("--serving-light-requests", type=int, default=16,
+                    help="requests of a second serving run under the GPU's capacity (0 skips)")
+    ap.add_argument("--serving-light-rate", type=float, default=2.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
