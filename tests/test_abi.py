@@ -157,3 +157,10 @@ def test_criterion_and_lookup_null_arguments(lib):
     assert lib.bn_evaluate_criterion(None, 0, 0, 1, None, 1, None) == L.BN_ERR_INVALID_ARG
     assert lib.bn_export_shift_table(None, 0, None, 0) == L.BN_ERR_INVALID_ARG
     assert lib.bn_generate_samples(None, 0, 0, 1, 1, 0, 1, 1, None, 0, 0) == L.BN_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the CUDA library there is no fallback: loading raises."""
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        L.load(str(tmp_path / "libbnsampler.so"))
