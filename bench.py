@@ -481,6 +481,69 @@ def run_ours(args) -> int:
     return 0
 
 
+def report_kernels(args) -> int:
+    """One timing of each kernel outside the sweep, on one 512 x 512 tile (N = 64, T = 1024,
+    256 MiB of counts): re-initialisation (dominated by the counts), Eq. 1, the criterion on
+    Heavisides and on bumps, and the renderer lookup for a 1920 x 1080 screen."""
+    import torch
+
+    import paper_2105_12620_gb300 as pkg
+    from paper_2105_12620_gb300 import build as pkg_build
+    pkg_build.build()
+    pkg.load()
+    W = H = 512
+    P = W * H
+    stream = torch.cuda.Stream()
+    s = pkg.Sampler(W, H, N_POINTS, T_INTEGRANDS, seed=1, sigma=SIGMA, radius=RADIUS,
+                    stream=stream)
+    energy = torch.empty(1, dtype=torch.float64, device="cuda")
+    SW, SH, NS = 1920, 1080, 16
+    samples = torch.empty(SW * SH * NS * 2, dtype=torch.float32, device="cuda")
+
+    def device_ms(fn, reps=3):
+        fn()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def host_ms(fn, reps=2):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return 1000 * (time.perf_counter() - t0) / reps
+
+    with torch.cuda.stream(stream):
+        t_init = device_ms(lambda: s.reset(1))
+        t_energy = device_ms(lambda: s.energy_into(energy.data_ptr()))
+        t_samples = device_ms(lambda: s.samples_into(samples.data_ptr(), samples.numel(), 0, 0,
+                                                     SW, SH, 0, NS, 2))
+    t_crit = host_ms(lambda: s.criterion([1.0, 4.0], "heaviside", 128))
+    t_bump = host_ms(lambda: s.criterion([1.0], "gaussian", 32))
+    s.close()
+    out = {
+        "report": "kernels outside the sweep", "tile": "512x512, N=64, T=1024 (256 MiB of int8 counts)",
+        "reinit": {"ms": t_init, "threshold_tests_per_s": P * N_POINTS * T_INTEGRANDS / t_init * 1e3,
+                   "note": "shifts, Heavisides, permutation, state, counts (P*N*T tests)"},
+        "energy": {"ms": t_energy,
+                   "bytes_per_s": P * STENCIL_OFFSETS * T_INTEGRANDS / t_energy * 1e3,
+                   "note": "one byte of a neighbour's counts per (pixel, offset, integrand), from L2"},
+        "criterion_heaviside": {"ms": t_crit, "integrands": 128, "sigmas": [1.0, 4.0],
+                                "note": "FP64, host call incl. scratch allocation"},
+        "criterion_bumps": {"ms": t_bump, "integrands": 32, "sigmas": [1.0],
+                            "note": "FP64, N exp per pixel and bump"},
+        "samples": {"ms": t_samples, "bytes_per_s": samples.numel() * 4 / t_samples * 1e3,
+                    "screen": f"{SW}x{SH}, {NS} samples, 2 dimensions"},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def report_modes(args) -> int:
     """Eq. 1 and the filtered error along the passes for the two commit rules on one 128 x 128
     tile: keep only non-interacting improving couples, or every improving couple (the paper's
@@ -535,8 +598,9 @@ def main(argv=None) -> int:
                     help="c2: 128x128 N=64 T=1024 tiles (default); c3: 256x256 N=256, two "
                          "pairs x T=512; c4: 96 mixed tiles")
     ap.add_argument("--sweeps", type=int, default=0, help="pass budget (0: the workload's)")
-    ap.add_argument("--report", choices=["modes"], default=None,
-                    help="modes: Eq. 1 along the passes for both commit rules (no timing)")
+    ap.add_argument("--report", choices=["modes", "kernels"], default=None,
+                    help="modes: Eq. 1 along the passes for both commit rules (no timing); "
+                         "kernels: one timing of each kernel outside the sweep")
     ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto")
     ap.add_argument("--cpu-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -559,6 +623,8 @@ def main(argv=None) -> int:
         raise SystemExit("--warmup must be >= 3")
     if args.report == "modes":
         return report_modes(args)
+    if args.report == "kernels":
+        return report_kernels(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

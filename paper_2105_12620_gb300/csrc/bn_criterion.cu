@@ -98,7 +98,7 @@ __global__ void k_err_heaviside(const Problem *probs, int first, int B, const do
     const int byte = (first + i) * (int)sizeof(CT);
     const CT k = reinterpret_cast<const CT *>(chunk_ptr(pb, p, byte >> 7))[(byte & 127) /
                                                                           (int)sizeof(CT)];
-    err[idx] = (double)k / (double)pb.N - ref[i];
+    err[idx] = (double)k * (1.0 / (double)pb.N) - ref[i];  // N = 2^m: exact, no division
 }
 
 // e[p][i] = (1/N) sum_k f_i(s_p^k) - ref_i for the bumps; one warp per pixel, lanes over bumps
@@ -121,7 +121,7 @@ __global__ void k_err_bumps(const Problem *probs, int B, const Bump *bank, doubl
             const double dx = x - bp.cx, dy = y - bp.cy;
             acc += exp(-(dx * dx + dy * dy) * bp.inv2s2);
         }
-        err[(size_t)p * B + i] = acc / (double)pb.N - bp.ref;
+        err[(size_t)p * B + i] = acc * (1.0 / (double)pb.N) - bp.ref;
     }
 }
 
