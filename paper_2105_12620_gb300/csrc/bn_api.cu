@@ -1206,14 +1206,19 @@ int autotune_entry(const std::vector<bn_sampler *> &members, const std::vector<b
             hit = true;
         }
     }
+    // a cached choice that no longer names a usable schedule (a cache file written by another
+    // build) is tuned again
+    if (hit && set_schedule_common(hp, dprob, &best, plan) != BN_OK) hit = false;
     if (!hit) {
         for (auto *m : members) BN_CUDA(cudaStreamSynchronize(m->stream));
         if (int rc = autotune(members, trial_sweeps, st, &best)) return rc;
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = best;
-        tune_file_store(key, best);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = best;
+            tune_file_store(key, best);
+        }
+        if (int rc = set_schedule_common(hp, dprob, &best, plan)) return rc;
     }
-    if (int rc = set_schedule_common(hp, dprob, &best, plan)) return rc;
     if (chosen) *chosen = best;
     return BN_OK;
 }

@@ -1231,15 +1231,19 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 cudaError_t encode_count_tensor_maps(const Problem &h, void *out)
 {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // looked up once per process (thread-safe static initialisation)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
-                                                         cudaEnableDefault, &q);
-        if (e != cudaSuccess) return e;
-        if (q != cudaDriverEntryPointSuccess || !ptr) return cudaErrorNotSupported;
-        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
+    if (!fn) {
+        cudaGetLastError();
+        return cudaErrorNotSupported;
     }
     // count planes [chunk][y][x][128 bytes]; a box is 8 pixels of 20, 14 or 6 rows, one chunk
     const cuuint64_t dims[4] = {(cuuint64_t)kChunk, (cuuint64_t)h.W, (cuuint64_t)h.H,
