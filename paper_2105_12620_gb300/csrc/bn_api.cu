@@ -110,8 +110,7 @@ struct SweepPlan {
     int total_units[2] = {0, 0}, total_couples[2] = {0, 0};
     int *d_prefix = nullptr;        // [2][2][n_prob + 1] unit / couple prefix sums
     bn::GridBarrier *d_bar = nullptr;
-    int *d_work = nullptr;          // [4] phase-1 unit counters, improving-list lengths
-    int2 *d_imp = nullptr;          // [2][max couples of a launch] improving-couple lists
+    int *d_work = nullptr;          // [2] phase-1 unit counters
     char *d_tmaps = nullptr;        // [n_prob] TMA tensor maps (tensor-core shape only)
     int n_prob = 0, max_M = 0, sms = 0;
     // plain schedule: passes per captured CUDA graph (0 = launch every kernel directly); the
@@ -133,8 +132,6 @@ void free_plan(SweepPlan &pl)
     if (pl.d_prefix) cudaFree(pl.d_prefix);
     if (pl.d_bar) cudaFree(pl.d_bar);
     if (pl.d_work) cudaFree(pl.d_work);
-    if (pl.d_imp) cudaFree(pl.d_imp);
-    pl.d_imp = nullptr;
     if (pl.d_tmaps) cudaFree(pl.d_tmaps);
     pl.d_prefix = nullptr;
     pl.d_bar = nullptr;
@@ -456,9 +453,7 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
     BN_CUDA(cudaMalloc(&pl.d_prefix, sizeof(int) * pre.size()));
     BN_CUDA(cudaMemcpy(pl.d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     BN_CUDA(cudaMalloc(&pl.d_bar, sizeof(bn::GridBarrier)));
-    BN_CUDA(cudaMalloc(&pl.d_work, 4 * sizeof(int)));
-    const int cap = std::max(pl.total_couples[0], pl.total_couples[1]);
-    BN_CUDA(cudaMalloc(&pl.d_imp, sizeof(int2) * 2 * (size_t)std::max(cap, 1)));
+    BN_CUDA(cudaMalloc(&pl.d_work, 2 * sizeof(int)));
     if (bn::persistent_shape_is_mma(pl.shape) && pl.count[0] > 0) {
         // tensor maps of the 8-bit problems' count planes, in problem order
         const size_t per = (size_t)bn::kTensorMapsPerProblem * bn::kTensorMapBytes;
@@ -532,15 +527,13 @@ int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Prob
         a.tsplit = pl.shape.tsplit;
         a.bar = pl.d_bar;
         a.work = pl.d_work;
-        a.imp = pl.d_imp;
-        a.imp_cap = pl.total_couples[g];
         a.tmaps = pl.d_tmaps ? pl.d_tmaps + (size_t)pl.first[g] * bn::kTensorMapsPerProblem *
                                                 bn::kTensorMapBytes
                              : nullptr;
         for (int32_t done = 0; done < n_sweeps; done += kItersPerLaunch) {
             a.n_iter = n_sweeps - done < kItersPerLaunch ? n_sweeps - done : kItersPerLaunch;
             BN_CUDA(cudaMemsetAsync(pl.d_bar, 0, sizeof(bn::GridBarrier), st));
-            BN_CUDA(cudaMemsetAsync(pl.d_work, 0, 4 * sizeof(int), st));
+            BN_CUDA(cudaMemsetAsync(pl.d_work, 0, 2 * sizeof(int), st));
             const bool timed = tm && tm->enabled;
             if (timed) tm->begin(bn::kKPersistent, st);
             cudaError_t e = bn::launch_persistent(a, pl.shape, g + 1, pl.sms, st);

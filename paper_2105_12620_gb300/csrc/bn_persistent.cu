@@ -1037,34 +1037,20 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
         }
         if (!grid_sync(args.bar, nblocks, &s_err)) break;
         // ---- phase 2: finalize (one thread per couple) ---------------------------------------
-        // counters of the next pass (their last readers finished before the previous barrier)
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            args.work[(it + 1) & 1] = 0;
-            args.work[2 + ((it + 1) & 1)] = 0;
-        }
-        int2 *imp_list = args.imp + (size_t)(it & 1) * args.imp_cap;
+        if (blockIdx.x == 0 && threadIdx.x == 0) args.work[(it + 1) & 1] = 0;
         for (int base = gwarp * 32; base < args.total_couples; base += nwarps * 32) {
             const int g = base + lane;
-            int pi = -1, j = 0;
+            int pi = -1;
             uint8_t f = 0;
             if (g < args.total_couples) {
                 pi = find_problem(args.couple_start, args.n_prob, g);
                 const Problem &pb = args.probs[pi];
                 const long long s = pb.ctr[0] + it;
-                j = g - __ldg(args.couple_start + pi);
                 if (s < pb.ctr[1])
-                    f = finalize_couple(pb, j, (uint32_t)s, args.tsplit);
+                    f = finalize_couple(pb, g - __ldg(args.couple_start + pi), (uint32_t)s,
+                                        args.tsplit);
                 else
                     pi = -1;
-            }
-            // improving couples go to the pass's list (one atomic per warp)
-            const unsigned im = __ballot_sync(0xFFFFFFFFu, (f & kFlagImproving) != 0);
-            if (im) {
-                int at = 0;
-                if (lane == 0) at = atomicAdd(args.work + 2 + (it & 1), __popc(im));
-                at = __shfl_sync(0xFFFFFFFFu, at, 0);
-                if (f & kFlagImproving)
-                    imp_list[at + __popc(im & ((1u << lane) - 1u))] = make_int2(pi, (j << 8) | f);
             }
             // warp-aggregated counters, one group of lanes per problem
             const unsigned grp = __match_any_sync(0xFFFFFFFFu, pi);
@@ -1080,15 +1066,34 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
         }
         if (!grid_sync(args.bar, nblocks, &s_err)) break;
         // ---- phase 3: resolve + commit -------------------------------------------------------
-        // the pass's improving couples, spread evenly over all warps
-        {
-            const int n_imp = __ldcg(args.work + 2 + (it & 1));
-            for (int k = gwarp; k < n_imp; k += nwarps) {
-                const int2 e = __ldcg(imp_list + k);
-                const Problem &pb = args.probs[e.x];
-                const uint32_t sw = (uint32_t)(pb.ctr[0] + it);
-                if (resolve_commit(pb, e.y >> 8, sw, (uint8_t)(e.y & 0xFF)) && lane == 0)
-                    atomicAdd(&pb.stats[kStatCommitted], 1ull);
+        // 32 couples per warp step: one flag load each, then the improving ones one by one
+        for (int base = gwarp * 32; base < args.total_couples; base += nwarps * 32) {
+            const int g = base + lane;
+            int pi = 0, j = 0;
+            uint8_t f = 0;
+            uint32_t sw = 0;
+            if (g < args.total_couples) {
+                pi = find_problem(args.couple_start, args.n_prob, g);
+                const Problem &pb = args.probs[pi];
+                const long long s = pb.ctr[0] + it;
+                if (s < pb.ctr[1]) {
+                    j = g - __ldg(args.couple_start + pi);
+                    sw = (uint32_t)s;
+                    f = (uint8_t)(__ldcg(reinterpret_cast<const unsigned int *>(pb.log_flags +
+                                                                               (j & ~3))) >>
+                                  (8 * (j & 3)));
+                }
+            }
+            unsigned m = __ballot_sync(0xFFFFFFFFu, (f & kFlagImproving) != 0);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1u;
+                const int lpi = __shfl_sync(0xFFFFFFFFu, pi, l);
+                const int lj = __shfl_sync(0xFFFFFFFFu, j, l);
+                const uint32_t lsw = __shfl_sync(0xFFFFFFFFu, sw, l);
+                const uint8_t lf = (uint8_t)__shfl_sync(0xFFFFFFFFu, (int)f, l);
+                if (resolve_commit(args.probs[lpi], lj, lsw, lf) && lane == 0)
+                    atomicAdd(&args.probs[lpi].stats[kStatCommitted], 1ull);
             }
         }
         if (!grid_sync(args.bar, nblocks, &s_err)) break;

@@ -27,10 +27,7 @@ struct PersistentArgs {
     int tsplit;
     int n_iter;             // passes in this launch (problems stop at their own pass end)
     GridBarrier *bar;
-    int *work;              // [4] by pass parity: phase-1 unit counters, then the lengths of
-                            // the improving-couple lists; zeroed per launch
-    int2 *imp;              // [2][imp_cap] improving couples of the pass: (problem, j << 8 | flags)
-    int imp_cap;            // list capacity: the launch's couple count
+    int *work;              // [2] unit counters of phase 1, by pass parity; zeroed per launch
     const char *tmaps;      // [n_prob][3] TMA tensor maps of the count planes, or null; used
                             // by the tensor-core variant
 };
