@@ -139,3 +139,54 @@ def test_cancel_pending_and_resident():
         assert st["cancelled"] == 2 and st["completed"] == 1 and st["memory_in_use"] == 0
         with pytest.raises(BnError):
             sv.cancel(12345)
+
+
+def test_concurrent_submitters_and_random_cancellations():
+    """Four threads submit at once while the loop runs; a random third of the requests is
+    cancelled.  Every request gets exactly one result; completed ones equal the request alone."""
+    import threading
+    rng = np.random.default_rng(5)
+    cfgs = [(int(rng.choice([24, 32, 40])), int(rng.choice([20, 32])), int(rng.choice([16, 64])),
+             64, 1, int(rng.integers(5, 40)), 200 + i) for i in range(24)]
+    with Server(max_slots=6, sweeps_per_chunk=4) as sv:
+        ids = [None] * len(cfgs)
+
+        def submit(part):
+            for k in part:
+                w, h, n, t, pairs, passes, seed = cfgs[k]
+                ids[k] = sv.submit(w, h, n, t, passes, seed=seed, n_pairs=pairs, user_tag=k)
+
+        threads = [threading.Thread(target=submit, args=(range(q, len(cfgs), 4),))
+                   for q in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        cancel = set(int(k) for k in rng.choice(len(cfgs), 8, replace=False))
+        for k in cancel:
+            try:
+                sv.cancel(ids[k])
+            except BnError:
+                pass   # already finished
+        sv.drain(300.0)
+        res = {r.user_tag: r for r in sv.poll(1024)}
+        assert sorted(res) == list(range(len(cfgs)))
+        st = sv.stats()
+        assert st["completed"] + st["cancelled"] == len(cfgs) and st["memory_in_use"] == 0
+        for k, r in res.items():
+            if r.status == L.BN_OK:
+                e_ref, sh_ref = alone(*cfgs[k])
+                np.testing.assert_array_equal(sv.take_shifts(r), sh_ref)
+                np.testing.assert_array_equal(np.asarray(r.energy), e_ref)
+            else:
+                assert r.status == L.BN_ERR_BAD_STATE and k in cancel
+
+
+def test_destroy_with_work_in_flight_returns():
+    sv = Server(max_slots=4, sweeps_per_chunk=10)
+    for k in range(6):
+        sv.submit(64, 64, 64, 512, 2000, seed=k)
+    time.sleep(0.2)
+    t0 = time.time()
+    sv.close()                      # drops queued and resident requests after the current chunk
+    assert time.time() - t0 < 30.0
