@@ -307,6 +307,9 @@ def workload_tiles(args):
     return tiles, desc
 
 
+SCHEDULE_NAMES = {1: "plain", 2: "persistent", 3: "tensor"}
+
+
 def run_ours(args) -> int:
     import torch
 
@@ -335,7 +338,8 @@ def run_ours(args) -> int:
     B = len(specs)
     sweeps = specs[0].sweeps  # every tile of a workload has the same pass budget
     schedule = {"auto": pkg.BN_SCHEDULE_AUTO, "plain": pkg.BN_SCHEDULE_PLAIN,
-                "persistent": pkg.BN_SCHEDULE_PERSISTENT}[args.schedule]
+                "persistent": pkg.BN_SCHEDULE_PERSISTENT,
+                "tensor": pkg.BN_SCHEDULE_TENSOR}[args.schedule]
     tiles = [pkg.Sampler(t.width, t.height, t.n_points, t.n_integrands,
                          seed=tile_seed(rank, 0, i, B), n_pairs=t.n_pairs, sigma=SIGMA,
                          radius=RADIUS, schedule=schedule, stream=stream)
@@ -480,8 +484,8 @@ def run_ours(args) -> int:
             "data": "synthetic",
             "config": {"workload": desc, "tiles_per_gpu": B, "sweeps": sweeps,
                        "schedule": args.schedule if chosen is None else
-                       {"kind": "persistent" if chosen["kind"] == pkg.BN_SCHEDULE_PERSISTENT
-                        else "plain", "block": chosen["shape"][:2],
+                       {"kind": SCHEDULE_NAMES.get(chosen["kind"], "?"),
+                        "block": chosen["shape"][:2],
                         "threads": chosen["shape"][2], "tsplit": chosen["tsplit"],
                         "chosen_by": chosen.get("chosen_by", "autotuner")},
                        "parallelism": f"independent tiles x{world}",
@@ -630,7 +634,8 @@ def main(argv=None) -> int:
     ap.add_argument("--report", choices=["modes", "kernels"], default=None,
                     help="modes: Eq. 1 along the passes for both commit rules (no timing); "
                          "kernels: one timing of each kernel outside the sweep")
-    ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto")
+    ap.add_argument("--schedule", choices=["auto", "plain", "persistent", "tensor"],
+                    default="auto")
     ap.add_argument("--cpu-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")

@@ -63,6 +63,9 @@ extern "C" {
 #define BN_SCHEDULE_AUTO 0       /* persistent when the tile allows it, else plain          */
 #define BN_SCHEDULE_PLAIN 1      /* three launches per sweep, one warp per couple           */
 #define BN_SCHEDULE_PERSISTENT 2 /* one cooperative launch for many sweeps, SMEM-blocked    */
+#define BN_SCHEDULE_TENSOR 3     /* five launches per sweep, the stencil of Eq. 1 as products */
+                                 /* on the 5th-generation tensor cores (8-bit counts, N <= 64,*/
+                                 /* tile sides >= 2 radius + 1)                               */
 
 typedef struct bn_config {
     int32_t width, height;     /* toroidal tile, 2..4096 each, width*height <= 2^22          */
@@ -211,13 +214,15 @@ typedef struct bn_schedule {
 int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc);
 int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out);
 
-/* Plain schedule: sweeps run as replays of a CUDA graph that holds passes_per_graph passes
- * (three kernels each), captured on first use; 0 launches every kernel directly.  Default 32.
+/* Plain and tensor-core schedules: sweeps run as replays of a CUDA graph that holds
+ * passes_per_graph passes (three or five kernels each), captured on first use; 0 launches every
+ * kernel directly.  Default 32.
  * Results are identical either way; per-kernel timing (bn_set_kernel_timing) bypasses the
  * graphs.  Synchronises the stream and drops graphs already captured. */
 int bn_sampler_set_graph_passes(bn_sampler *s, int32_t passes_per_graph);
 
-/* Autotuner: time every instantiated schedule (CTA shape x chunk split, plain as fallback) for
+/* Autotuner: time every instantiated schedule (CTA shape x chunk split, the tensor-core
+ * schedule where every tile allows it, plain as fallback) for
  * trial_sweeps passes on a scratch copy of the device state, keep the fastest, and cache the
  * choice per workload signature (tile sizes, N, T, couples, radius, SM count) in the process and,
  * when the environment variable BN_AUTOTUNE_CACHE names a file, in that file.  The caller's

@@ -7,5 +7,5 @@ The computation lives in ``libbnsampler.so`` (CUDA, sm_103a), reached through th
 from ._lib import (BN_MODE_CONCURRENT, BN_MODE_NONINTERACTING, BN_OBJECTIVE_BLUE,  # noqa: F401
                    BN_INTEGRANDS_GAUSSIAN, BN_INTEGRANDS_HEAVISIDE,
                    BN_OBJECTIVE_LITERAL, BN_SCHEDULE_AUTO, BN_SCHEDULE_PERSISTENT,
-                   BN_SCHEDULE_PLAIN, BnError, load)
+                   BN_SCHEDULE_PLAIN, BN_SCHEDULE_TENSOR, BnError, load)
 from .sampler import Batch, Result, Sampler, Server, SweepStats  # noqa: F401

@@ -19,7 +19,7 @@ BN_ERR_INVALID_ARG, BN_ERR_OOM, BN_ERR_CUDA, BN_ERR_TIMEOUT, BN_ERR_BUSY, BN_ERR
     -1, -2, -3, -4, -5, -6)
 BN_MODE_NONINTERACTING, BN_MODE_CONCURRENT = 0, 1
 BN_OBJECTIVE_BLUE, BN_OBJECTIVE_LITERAL = -1, 1
-BN_SCHEDULE_AUTO, BN_SCHEDULE_PLAIN, BN_SCHEDULE_PERSISTENT = 0, 1, 2
+BN_SCHEDULE_AUTO, BN_SCHEDULE_PLAIN, BN_SCHEDULE_PERSISTENT, BN_SCHEDULE_TENSOR = 0, 1, 2, 3
 BN_INTEGRANDS_HEAVISIDE, BN_INTEGRANDS_GAUSSIAN = 0, 1
 
 

@@ -104,6 +104,9 @@ namespace {
 // How the passes of a set of problems are executed, and the device arrays that go with it.
 struct SweepPlan {
     bool persistent = false;
+    bool tensor = false;            // tensor-core schedule (every problem has 8-bit counts)
+    int *d_tc_prefix = nullptr;     // [n_prob + 1] prefix sums of 16 x 8 patches
+    int tc_units = 0;
     bn::PersistentShape shape{8, 8, 256, 4, 0};
     // per count width (index cb - 1): first problem, problem count, units / couples prefix
     int first[2] = {0, 0}, count[2] = {0, 0};
@@ -133,6 +136,11 @@ void free_plan(SweepPlan &pl)
     if (pl.d_bar) cudaFree(pl.d_bar);
     if (pl.d_work) cudaFree(pl.d_work);
     if (pl.d_tmaps) cudaFree(pl.d_tmaps);
+    if (pl.d_tc_prefix) cudaFree(pl.d_tc_prefix);
+    pl.d_tc_prefix = nullptr;
+    pl.tensor = false;
+    pl.persistent = false;
+    pl.tc_units = 0;
     pl.d_prefix = nullptr;
     pl.d_bar = nullptr;
     pl.d_work = nullptr;
@@ -212,7 +220,7 @@ int validate(const bn_config &c)
         return fail(BN_ERR_INVALID_ARG, "unknown mode %d", c.mode);
     if (c.objective != 0 && c.objective != BN_OBJECTIVE_BLUE && c.objective != BN_OBJECTIVE_LITERAL)
         return fail(BN_ERR_INVALID_ARG, "unknown objective %d", c.objective);
-    if (c.schedule < BN_SCHEDULE_AUTO || c.schedule > BN_SCHEDULE_PERSISTENT)
+    if (c.schedule < BN_SCHEDULE_AUTO || c.schedule > BN_SCHEDULE_TENSOR)
         return fail(BN_ERR_INVALID_ARG, "unknown schedule %d", c.schedule);
     return BN_OK;
 }
@@ -293,6 +301,11 @@ void carve(Slab &s, bn::Problem &h)
     h.log_flags = s.take<uint8_t>((size_t)h.M + 4);  // phase 2 reads aligned 4-byte words
     h.log_couples = s.take<int32_t>((size_t)h.M * 2);
     h.side_cls = s.take<int32_t>((size_t)h.M * 2 * bn::kMaxTsplit * bn::kMaxClasses);
+    h.tc_npx = (h.W + 15) / 16;
+    h.tc_npy = (h.H + 7) / 8;
+    h.tc_cap = (16 + 2 * h.radius) * (8 + 2 * h.radius);
+    h.tc_cnt = s.take<int32_t>((size_t)h.tc_npx * h.tc_npy);
+    h.tc_list = s.take<int32_t>((size_t)h.tc_npx * h.tc_npy * h.tc_cap);
     h.ctr = s.take<long long>(4);
     h.stats = s.take<unsigned long long>(bn::kStatCount);
     h.esum = s.take<unsigned long long>(bn::kMaxClasses);
@@ -378,6 +391,24 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
     int dev = 0;
     BN_CUDA(cudaGetDevice(&dev));
     BN_CUDA(cudaDeviceGetAttribute(&pl.sms, cudaDevAttrMultiProcessorCount, dev));
+    if (schedule == BN_SCHEDULE_TENSOR) {
+        for (auto &h : hp)
+            if (!bn::tc_supported(h))
+                return fail(BN_ERR_INVALID_ARG, "the tensor-core schedule needs 8-bit counts "
+                            "(N <= 64) and tile sides of at least 2 radius + 1");
+        std::vector<int> pre((size_t)pl.n_prob + 1, 0);
+        for (int i = 0; i < pl.n_prob; ++i) pre[i + 1] = pre[i] + bn::tc_units_per_problem(hp[i]);
+        pl.tc_units = pre[pl.n_prob];
+        BN_CUDA(bn::prepare_tc());
+        BN_CUDA(cudaMalloc(&pl.d_tc_prefix, sizeof(int) * pre.size()));
+        BN_CUDA(cudaMemcpy(pl.d_tc_prefix, pre.data(), sizeof(int) * pre.size(),
+                           cudaMemcpyHostToDevice));
+        pl.tensor = true;
+        pl.first[0] = 0;
+        pl.count[0] = pl.n_prob;
+        pl.first[1] = pl.count[1] = 0;
+        return BN_OK;
+    }
     bool ok = true;
     for (auto &h : hp) ok = ok && bn::persistent_supported(h);
     if (schedule == BN_SCHEDULE_PERSISTENT && !ok)
@@ -470,16 +501,34 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
 
 constexpr int kItersPerLaunch = 500;
 
-// Capture graph_passes passes of the plain schedule (three launches each) as one CUDA graph.
-// Every kernel reads the pass index and budget from device memory, so the graph replays.
+int plan_kind(const SweepPlan &pl)
+{
+    return pl.tensor ? BN_SCHEDULE_TENSOR
+                     : (pl.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN);
+}
+
+// one pass of the plain or tensor-core schedule (three or five launches)
+cudaError_t launch_pass(const SweepPlan &pl, const bn::SweepLaunch &sl, cudaStream_t st,
+                        bn::KernelTimer *tm)
+{
+    if (!pl.tensor) return bn::launch_plain_sweep(sl, st, tm);
+    const bn::TcLaunch tl{sl.dprob, sl.n_prob, pl.max_M, pl.d_tc_prefix, pl.tc_units, pl.sms};
+    return bn::launch_tc_sweep(tl, st, tm);
+}
+
+int launches_per_pass(const SweepPlan &pl) { return pl.tensor ? 5 : 3; }
+
+// Capture graph_passes passes of the plain or tensor-core schedule as one CUDA graph.  Every
+// kernel reads the pass index and budget from device memory, so the graph replays.
 int capture_plain(SweepPlan &pl, const bn::SweepLaunch &sl, int g)
 {
     if (!pl.capture) BN_CUDA(cudaStreamCreateWithFlags(&pl.capture, cudaStreamNonBlocking));
     BN_CUDA(cudaStreamBeginCapture(pl.capture, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
+    const long long before = bn::launch_count();
     for (int k = 0; k < pl.graph_passes && e == cudaSuccess; ++k)
-        e = bn::launch_plain_sweep(sl, pl.capture, nullptr);
-    bn::note_launches(-3ll * pl.graph_passes);  // captured, not launched
+        e = launch_pass(pl, sl, pl.capture, nullptr);
+    bn::note_launches(before - bn::launch_count());  // captured, not launched
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(pl.capture, &graph);
     if (e == cudaSuccess) e = e2;
@@ -487,7 +536,7 @@ int capture_plain(SweepPlan &pl, const bn::SweepLaunch &sl, int g)
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         pl.graph[g] = nullptr;
-        return fail(BN_ERR_CUDA, "capture of the plain sweep graph failed: %s",
+        return fail(BN_ERR_CUDA, "capture of the sweep graph failed: %s",
                     cudaGetErrorString(e));
     }
     return BN_OK;
@@ -509,9 +558,10 @@ int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Prob
                     if (int rc = capture_plain(pl, sl, g)) return rc;
                 for (; k + pl.graph_passes <= n_sweeps; k += pl.graph_passes)
                     BN_CUDA(cudaGraphLaunch(pl.graph[g], st));
-                bn::note_launches(3ll * pl.graph_passes * ((n_sweeps / pl.graph_passes)));
+                bn::note_launches((long long)launches_per_pass(pl) * pl.graph_passes *
+                                  ((n_sweeps / pl.graph_passes)));
             }
-            for (; k < n_sweeps; ++k) BN_CUDA(bn::launch_plain_sweep(sl, st, tm));
+            for (; k < n_sweeps; ++k) BN_CUDA(launch_pass(pl, sl, st, tm));
         }
         return BN_OK;
     }
@@ -613,7 +663,7 @@ int bn_sampler_init(const bn_config *cfg, void *cuda_stream, bn_sampler **out)
         bn_sampler_destroy(s);
         return fail(rc2, "%s", msg.c_str());
     }
-    s->schedule = s->plan.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    s->schedule = plan_kind(s->plan);
     *out = s;
     return BN_OK;
 }
@@ -1010,7 +1060,7 @@ static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Pro
 {
     if (!sc) return fail(BN_ERR_INVALID_ARG, "null schedule");
     if (sc->kind != BN_SCHEDULE_PLAIN && sc->kind != BN_SCHEDULE_PERSISTENT &&
-        sc->kind != BN_SCHEDULE_AUTO)
+        sc->kind != BN_SCHEDULE_AUTO && sc->kind != BN_SCHEDULE_TENSOR)
         return fail(BN_ERR_INVALID_ARG, "unknown schedule kind %d", sc->kind);
     bn::PersistentShape shape{sc->block_x, sc->block_y, sc->threads, sc->slots_per_warp,
                               sc->tsplit};
@@ -1020,7 +1070,8 @@ static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Pro
                       shape.spw == SPW);
     BN_PERSISTENT_SHAPES(BN_KNOWN)
 #undef BN_KNOWN
-    const bool want_shape = sc->kind != BN_SCHEDULE_PLAIN && sc->block_x > 0;
+    const bool want_shape = (sc->kind == BN_SCHEDULE_PERSISTENT || sc->kind == BN_SCHEDULE_AUTO) &&
+                            sc->block_x > 0;
     if (want_shape && !known)
         return fail(BN_ERR_INVALID_ARG, "no kernel instantiated for block %dx%d, %d threads, %d "
                     "slots per warp", sc->block_x, sc->block_y, sc->threads, sc->slots_per_warp);
@@ -1029,7 +1080,7 @@ static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Pro
 
 static void get_schedule_common(const SweepPlan &pl, bn_schedule *out)
 {
-    out->kind = pl.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    out->kind = plan_kind(pl);
     out->block_x = pl.shape.bx;
     out->block_y = pl.shape.by;
     out->threads = pl.shape.threads;
@@ -1092,7 +1143,8 @@ void rebase(bn::Problem &h, const char *from, char *to)
     };
     mv(h.counts); mv(h.U); mv(h.sidx); mv(h.perm); mv(h.perm_inv); mv(h.ha); mv(h.hb);
     mv(h.hC); mv(h.owner); mv(h.log_dE); mv(h.log_flags); mv(h.log_couples);
-    mv(h.side_cls); mv(h.ctr); mv(h.stats); mv(h.esum); mv(h.energy_out);
+    mv(h.side_cls); mv(h.tc_cnt); mv(h.tc_list); mv(h.ctr); mv(h.stats); mv(h.esum);
+    mv(h.energy_out);
 }
 
 // Time every candidate schedule on a scratch copy of the members; returns the fastest.
@@ -1149,19 +1201,24 @@ int autotune(const std::vector<bn_sampler *> &members, int32_t trial_sweeps, cud
                                                                 (NCW + 1) * 32, SPW, ts});
     BN_PERSISTENT_SHAPES(BN_CAND)
 #undef BN_CAND
+    cands.push_back(bn_schedule{BN_SCHEDULE_TENSOR, 0, 0, 0, 0, 0});
     cands.push_back(bn_schedule{BN_SCHEDULE_PLAIN, 0, 0, 0, 0, 0});
     float best_ms = -1.f;
     for (const auto &c : cands) {
         bn::PersistentShape shape{c.block_x, c.block_y, c.threads, c.slots_per_warp, c.tsplit};
         bool fits = c.kind == BN_SCHEDULE_PLAIN;
-        if (!fits) {
+        if (c.kind == BN_SCHEDULE_TENSOR) {
+            fits = true;
+            for (const auto &h : hp) fits = fits && bn::tc_supported(h);
+        } else if (!fits) {
             fits = true;
             for (const auto &h : hp)
                 fits = fits && bn::persistent_shape_fits(h, shape) && h.row_bytes / 128 >= c.tsplit;
         }
         if (!fits) continue;
         if (c.kind == BN_SCHEDULE_PLAIN && best_ms >= 0.f) continue;  // plain only as fallback
-        if ((rc = make_plan(hp, dp, c.kind, c.kind == BN_SCHEDULE_PLAIN ? nullptr : &shape, plan)))
+        if ((rc = make_plan(hp, dp, c.kind, c.kind == BN_SCHEDULE_PERSISTENT ? &shape : nullptr,
+                            plan)))
             break;
         if ((rc = run_plan(plan, dp, hp, 2, st, nullptr))) break;  // warm
         cudaEventRecord(e0, st);
@@ -1242,7 +1299,7 @@ int bn_sampler_autotune(bn_sampler *s, int32_t trial_sweeps, bn_schedule *chosen
     if (int rc = set_device(s)) return rc;
     if (int rc = autotune_entry({s}, s->hprob, s->dprob, s->stream, trial_sweeps, s->plan, chosen))
         return rc;
-    s->schedule = s->plan.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    s->schedule = plan_kind(s->plan);
     return BN_OK;
 }
 
@@ -1252,7 +1309,7 @@ int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc)
     if (int rc = set_device(s)) return rc;
     BN_CUDA(cudaStreamSynchronize(s->stream));
     if (int rc = set_schedule_common(s->hprob, s->dprob, sc, s->plan)) return rc;
-    s->schedule = s->plan.persistent ? BN_SCHEDULE_PERSISTENT : BN_SCHEDULE_PLAIN;
+    s->schedule = plan_kind(s->plan);
     return BN_OK;
 }
 
@@ -1366,8 +1423,12 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
         return fail(BN_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
     }
     int sched = BN_SCHEDULE_AUTO;
-    for (int i = 0; i < n; ++i)
+    bool all_tensor = true;
+    for (int i = 0; i < n; ++i) {
         if (samplers[i]->cfg.schedule == BN_SCHEDULE_PLAIN) sched = BN_SCHEDULE_PLAIN;
+        all_tensor = all_tensor && samplers[i]->cfg.schedule == BN_SCHEDULE_TENSOR;
+    }
+    if (all_tensor && sched == BN_SCHEDULE_AUTO) sched = BN_SCHEDULE_TENSOR;
     b->all = all;
     if (int rc = make_plan(b->all, b->dprob, sched, nullptr, b->plan)) {
         std::string msg = g_error;

@@ -10,6 +10,7 @@
 //   perm     int32  [2^L]     candidate permutation (Sec. 3.4), perm_inv its inverse
 //   ha, hb   int32  [T], hC int64 [T]  Heaviside [a x + b y < c], C = c * 2^24
 //   owner    uint64 [2][P]    per-pass claim of a pixel by an improving couple (by parity)
+//   tc_cnt, tc_list           per-pass lists of the proposed pixels near each 16 x 8 patch
 //   log_*    [M]              last pass: change of Eq. 1, flags, couple pixels
 //   ctr      int64 [4]        pass counter, pass end, launch ticket, spare
 #pragma once
@@ -57,7 +58,11 @@ struct Problem {
     float *log_dE;
     uint8_t *log_flags;
     int32_t *log_couples;
-    int32_t *side_cls;         // [M][2 x tsplit][kMaxClasses] partial class sums (persistent)
+    int32_t *side_cls;         // [M][2 x tsplit][kMaxClasses] partial class sums (persistent);
+                               // [2 M][kMaxClasses] per proposed pixel (tensor-core schedule)
+    int32_t *tc_cnt;           // [tc_npx * tc_npy] proposed pixels listed per patch
+    int32_t *tc_list;          // [tc_npx * tc_npy][tc_cap] their slots 2 j + side
+    int32_t tc_npx, tc_npy, tc_cap;  // patches of 16 x 8 pixels per row / column, list capacity
     long long *ctr;            // [0] pass counter, [1] pass end, [2] ticket
     unsigned long long *stats; // [kStatCount]
     unsigned long long *esum;  // [kMaxClasses] energy class sums (two's complement int64)
@@ -254,6 +259,25 @@ __device__ __forceinline__ void renorm(F2 &s)
     const float t = s.hi + s.lo;
     s.lo = s.lo - (t - s.hi);
     s.hi = t;
+}
+
+
+// fp32 change of Eq. 1 from the exact class sums; also the sum of absolute terms
+__device__ __forceinline__ void couple_delta(const Problem &pb, const int *A, float &dL,
+                                             float &S)
+{
+    F2 acc = {0.f, 0.f};
+    float sabs = 0.f;
+#pragma unroll
+    for (int c = 0; c < kMaxClasses; ++c) {
+        if (c < pb.n_cls) {
+            add_weighted_i32(acc, pb.w[c], A[c]);
+            sabs += pb.w[c] * fabsf((float)A[c]);
+        }
+    }
+    renorm(acc);
+    dL = -pb.scale * acc.hi;
+    S = pb.scale * sabs;
 }
 
 }  // namespace bn

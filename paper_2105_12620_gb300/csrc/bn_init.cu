@@ -73,6 +73,7 @@ __global__ void k_clear_state(const Problem *probs)
     if (i < 2 * pb.P) pb.owner[i] = 0ull;
     if (i < kStatCount) pb.stats[i] = 0ull;
     if (i < 4) pb.ctr[i] = 0;
+    if (i < pb.tc_npx * pb.tc_npy) pb.tc_cnt[i] = 0;
 }
 
 // Counting kernel (Sec. 2 and Sec. 3.2): k_p[t] = #{k < N : a_t X + b_t Y < C_t} with

@@ -48,7 +48,7 @@ cudaError_t launch_energy_copy(const Problem *dprob, int n_prob, double *dev_out
 
 // Optional CUDA-event bracketing of kernel launches (host side).
 enum KernelKind { kKEvalPlain = 0, kKResolvePlain, kKCommitPlain, kKPersistent, kKEnergy,
-                  kKCounts, kKindCount };
+                  kKCounts, kKTcStencil, kKindCount };
 extern const char *const kKernelNames[kKindCount];
 
 struct KernelTimer {
@@ -77,9 +77,25 @@ struct SweepLaunch {
     int count_bytes;        // 1 or 2 (all problems of one launch share it)
 };
 cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm);
+// resolve + commit of the plain schedule alone
+cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st);
 cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int reset_stats,
                            cudaStream_t st);
 cudaError_t launch_set_ends(const Problem *dprob, int n_prob, const int *n_sweeps_dev,
                             int reset_stats, cudaStream_t st);
+
+// tensor-core schedule (bn_tc.cu): 8-bit counts, radius <= 8, tile sides >= 2 radius + 1
+struct TcLaunch {
+    const Problem *dprob;   // device array of problems (all with 8-bit counts)
+    int n_prob;
+    int max_M;
+    const int *unit_start;  // device [n_prob + 1] prefix sums of 16 x 8 patches
+    int total_units;
+    int sms;
+};
+bool tc_supported(const Problem &h);
+int tc_units_per_problem(const Problem &h);
+cudaError_t prepare_tc();
+cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm);
 
 }  // namespace bn

@@ -27,24 +27,6 @@ __device__ __forceinline__ int warp_sum(int v)
     return v;
 }
 
-// fp32 change of Eq. 1 from the exact class sums; also the sum of absolute terms
-__device__ __forceinline__ void couple_delta(const Problem &pb, const int *A, float &dL,
-                                             float &S)
-{
-    F2 acc = {0.f, 0.f};
-    float sabs = 0.f;
-#pragma unroll
-    for (int c = 0; c < kMaxClasses; ++c) {
-        if (c < pb.n_cls) {
-            add_weighted_i32(acc, pb.w[c], A[c]);
-            sabs += pb.w[c] * fabsf((float)A[c]);
-        }
-    }
-    renorm(acc);
-    dL = -pb.scale * acc.hi;
-    S = pb.scale * sabs;
-}
-
 template <int CB>
 __global__ void __launch_bounds__(kPlainThreads) k_eval_plain(const Problem *probs)
 {
@@ -269,9 +251,21 @@ cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTim
     return cudaGetLastError();
 }
 
+// the resolve and commit kernels alone (the tensor-core schedule evaluates couples itself)
+cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st)
+{
+    dim3 grid((sl.max_M + kPlainWarps - 1) / kPlainWarps, sl.n_prob);
+    k_resolve_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
+    k_commit_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
 // ---- kernel timer ---------------------------------------------------------------------------
-const char *const kKernelNames[kKindCount] = {"eval_plain", "resolve_plain", "commit_plain",
-                                               "sweep_persistent", "energy", "counts"};
+const char *const kKernelNames[kKindCount] = {"eval_plain",       "resolve_plain",
+                                               "commit_plain",     "sweep_persistent",
+                                               "energy",           "counts",
+                                               "stencil_tensor"};
 
 cudaEvent_t KernelTimer::get()
 {

@@ -106,7 +106,8 @@ class Sampler:
         L.check(L.load().bn_sampler_set_schedule(self._h, ctypes.byref(sc)))
 
     def set_graph_passes(self, passes: int) -> None:
-        """Plain schedule: passes per captured CUDA graph (0 = direct launches)."""
+        """Plain and tensor-core schedules: passes per captured CUDA graph (0 = direct
+        launches)."""
         L.check(L.load().bn_sampler_set_graph_passes(self._h, passes))
 
     def get_schedule(self) -> dict:
