@@ -305,7 +305,7 @@ void carve(Slab &s, bn::Problem &h)
     h.tc_npy = (h.H + 7) / 8;
     h.tc_cap = (16 + 2 * h.radius) * (8 + 2 * h.radius);
     h.tc_cnt = s.take<int32_t>((size_t)h.tc_npx * h.tc_npy);
-    h.tc_list = s.take<int32_t>((size_t)h.tc_npx * h.tc_npy * h.tc_cap);
+    h.tc_list = s.take<int4>((size_t)h.tc_npx * h.tc_npy * h.tc_cap);
     h.ctr = s.take<long long>(4);
     h.stats = s.take<unsigned long long>(bn::kStatCount);
     h.esum = s.take<unsigned long long>(bn::kMaxClasses);

@@ -61,7 +61,8 @@ struct Problem {
     int32_t *side_cls;         // [M][2 x tsplit][kMaxClasses] partial class sums (persistent);
                                // [2 M][kMaxClasses] per proposed pixel (tensor-core schedule)
     int32_t *tc_cnt;           // [tc_npx * tc_npy] proposed pixels listed per patch
-    int32_t *tc_list;          // [tc_npx * tc_npy][tc_cap] their slots 2 j + side
+    int4 *tc_list;             // [tc_npx * tc_npy][tc_cap] (pixel, partner, slot 2 j + side,
+                               // position relative to the patch centre), see bn_tc.cu
     int32_t tc_npx, tc_npy, tc_cap;  // patches of 16 x 8 pixels per row / column, list capacity
     long long *ctr;            // [0] pass counter, [1] pass end, [2] ticket
     unsigned long long *stats; // [kStatCount]

@@ -8,7 +8,7 @@
 // i.e. selected entries of the product D = K . Delta^T of count vectors (rows q) and deltas
 // (rows n).  The tile is cut into patches of 16 x 8 pixels.  Per patch the tensor core forms
 // D[q][n] for the patch's 128 pixels q (M = 128) and the proposed pixels n within the weight
-// radius of it (the patch's list, at most 192 per product), accumulating over all T integrands
+// radius of it (the patch's list, at most 160 per product), accumulating over all T integrands
 // in tensor memory; about a fifth of the entries lie inside the radius and are kept.  The f16
 // operands are exact (counts <= 64, |delta| <= 64) and the f32 sums stay within 2^24
 // (T N^2 <= 2^24 for 8-bit counts), so every kept entry is an exact integer.
@@ -17,18 +17,21 @@
 //   k_tc_lists     couples of the pass as in the plain schedule; each proposed pixel is appended
 //                  to the list of every patch within the radius of it; its class sums cleared
 //   k_tc_stencil   one CTA per SM over the patches, warp-specialised:
-//                    8 producer warps   count bytes -> shared memory (cp.async), converted in
+//                    9 producer warps   count bytes -> shared memory (cp.async), converted in
 //                                       place to f16 in the 128-byte swizzled K-major layout,
-//                                       deltas formed on the way; stages of 64 integrands
+//                                       deltas formed on the way; one row of every stage per
+//                                       thread; stages of 64 integrands
 //                    1 MMA warp         four tcgen05.mma (K = 16 each) per stage
 //                    4 epilogue warps   tensor memory -> registers; entries inside the radius
 //                                       go to per-pixel class sums in shared memory, then to
 //                                       the global class sums (integer atomics)
-//                  four stages in a ring, two accumulator buffers in tensor memory
+//                  five stages in a ring, two accumulator buffers in tensor memory
 //   k_tc_finalize  change of Eq. 1 from the class sums, flags and pixel claims
 //   then the resolve and commit kernels of the plain schedule.
 // Every wait is bounded; a wait that runs out raises the problems' error word and the CTA
 // drains its copies and products, frees its tensor memory and returns.
+#include <utility>
+
 #include "bn_launch.h"
 #include "bn_tcgen05.cuh"
 
@@ -36,27 +39,37 @@ namespace bn {
 namespace {
 
 constexpr int kPW = 16, kPH = 8, kTcM = kPW * kPH;  // patch: M = 128 pixels
-constexpr int kNB = 192;                             // listed pixels per product (N)
-constexpr int kStages = 4;                           // ring of 64-integrand stages
-constexpr int kLook = 2;                             // stages in flight per producer thread
+constexpr int kNB = 160;                             // listed pixels per product (N)
+constexpr int kStages = 5;                           // ring of 64-integrand stages
+constexpr int kLook = 3;                             // stages in flight per producer thread
 constexpr int kAStage = kTcM * 128;                  // 16 KB: 128 rows x 64 f16
-constexpr int kBStage = kNB * 128;                   // 24 KB: 192 rows x 64 f16
+constexpr int kBStage = kNB * 128;                   // 20 KB: 160 rows x 64 f16
 constexpr int kStageBytes = kAStage + kBStage;
-constexpr int kEpiWarps = 4, kProdWarps = 8;
+constexpr int kEpiWarps = 4, kProdWarps = (kTcM + kNB) / 32;  // one producer thread per row
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
-constexpr int kTcThreads = (kMmaWarp + 1) * 32;      // 416
+constexpr int kTcThreads = (kMmaWarp + 1) * 32;      // 448
 constexpr uint32_t kTmemCols = 512, kTmemBuf = 256;  // two accumulator buffers
 constexpr int kTabMax = 65;                          // squared distances 0..64 (radius <= 8)
 constexpr long long kSpin = 1ll << 31;               // ~1 s at 2 GHz
 constexpr unsigned long long kErrTc = 3ull;
+constexpr int kFlushBatch = 5;                       // class-sum rows sent per batch
 
 // shared memory layout (offsets from a 1024-byte aligned base)
-constexpr int kOffAcc = kStages * kStageBytes;        // int32 [kNB][32] class sums
-constexpr int kOffCol = kOffAcc + kNB * 32 * 4;       // int4  [kNB] (x, y, partner, slot)
-constexpr int kOffTab = kOffCol + kNB * 16;           // int32 [80] class of a squared distance
-constexpr int kOffBar = kOffTab + 80 * 4;             // mbarriers
+// epilogue scratch: int32 [kNB][32] class sums (lane-per-pixel paths), or a 32-column transpose
+// of the accumulators, float [32][128], and per-warp partial class sums, int32 [4][32][33]
+// (column-per-thread path)
+constexpr int kOffAcc = kStages * kStageBytes;
+constexpr int kOffPart = kOffAcc + 32 * kTcM * 4;
+constexpr int kEpiScratch = kNB * 32 * 4 > 32 * kTcM * 4 + 4 * 32 * 33 * 4
+                                ? kNB * 32 * 4
+                                : 32 * kTcM * 4 + 4 * 32 * 33 * 4;
+constexpr int kOffCol = kOffAcc + kEpiScratch;        // int4 [2][kNB] per listed pixel
+constexpr int kOffTab = kOffCol + 2 * kNB * 16;       // int32 [80] class of a squared distance
+constexpr int kOffTab2 = kOffTab + 80 * 4;            // int8 [2-D offset] class (fast path)
+constexpr int kTab2Max = 1664;                        // (2 (16 + 8) + 1) x (2 (8 + 8) + 1)
+constexpr int kOffBar = kOffTab2 + kTab2Max;          // mbarriers
 constexpr int kNBars = 2 * kStages + 5;
 constexpr int kOffMisc = kOffBar + kNBars * 8;        // tensor-memory base, abort flag
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;
@@ -108,6 +121,12 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
         }
     }
 }
+// integer add to global memory without a return value
+__device__ __forceinline__ void red_add_global(int32_t *p, int v)
+{
+    // no compiler memory barrier: nothing in the kernel reads these sums
+    asm volatile("red.global.add.s32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v));
+}
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
@@ -154,8 +173,8 @@ __device__ __forceinline__ int find_problem(const int *start, int n, int u)
     return lo;
 }
 
-// four bytes -> two f16x2 (bytes 0,1 and 2,3); the bytes are read as 1024 + byte and bias
-// (1024, or 1152 for deltas stored offset by 128) is subtracted, so the values are exact
+// four bytes -> two f16x2 (bytes 0,1 and 2,3); the bytes are read as 1024 + byte and 1024 is
+// subtracted, so the values are exact
 __device__ __forceinline__ void bytes_to_h2(uint32_t x, uint32_t bias2, uint32_t &lo, uint32_t &hi)
 {
     const uint32_t a = __byte_perm(x, 0x64646464u, 0x4140);
@@ -164,14 +183,22 @@ __device__ __forceinline__ void bytes_to_h2(uint32_t x, uint32_t bias2, uint32_t
     asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(b), "r"(bias2));
 }
 constexpr uint32_t kBiasCount = 0x64006400u;  // f16x2 (1024, 1024)
-constexpr uint32_t kBiasDelta = 0x64806480u;  // f16x2 (1152, 1152)
+// four byte differences a - b -> two f16x2: both read as 1024 + byte, then subtracted
+__device__ __forceinline__ void bytes_sub_h2(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi)
+{
+    const uint32_t a0 = __byte_perm(a, 0x64646464u, 0x4140);
+    const uint32_t a1 = __byte_perm(a, 0x64646464u, 0x4342);
+    const uint32_t b0 = __byte_perm(b, 0x64646464u, 0x4140);
+    const uint32_t b1 = __byte_perm(b, 0x64646464u, 0x4342);
+    asm("sub.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(a0), "r"(b0));
+    asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(a1), "r"(b1));
+}
 
 // The unit decode shared by the three roles: the same global sequence of patches and of
 // products (jobs) on every role, from values that do not change during the launch.
 struct Unit {
     const Problem *pb;
     int pid, cnt, x0, y0;
-    uint32_t xs;
 };
 __device__ __forceinline__ Unit decode_unit(const TcArgs &args, int u, int &pi)
 {
@@ -189,26 +216,86 @@ __device__ __forceinline__ Unit decode_unit(const TcArgs &args, int u, int &pi)
     d.cnt = c;
     d.x0 = (d.pid % pb.tc_npx) * kPW;
     d.y0 = (d.pid / pb.tc_npx) * kPH;
-    d.xs = pass_xor(pb, (uint32_t)s);
     return d;
 }
 
-// proposed pixel and partner of a listed slot 2 j + side
-__device__ __forceinline__ void slot_pixels(const Problem &pb, uint32_t xs, int slot, int &p,
-                                            int &partner)
+// 2-D class table of the epilogue's fast path: offsets (dx, dy) from a proposed pixel to a patch
+// pixel, |dx| <= 16 + r, |dy| <= 8 + r, row-major with row length 2 (16 + r) + 1
+__host__ __device__ __forceinline__ int tab2_dx(int r) { return 16 + r; }
+__host__ __device__ __forceinline__ int tab2_dy(int r) { return 8 + r; }
+__host__ __device__ __forceinline__ int tab2_w(int r) { return 2 * (16 + r) + 1; }
+// the fast path holds when the torus is wide enough that a proposed pixel's offset from the patch
+// centre, taken as the min-image, is its true offset (below half a side): W > 2 (8 + r),
+// H > 2 (4 + r)
+__host__ __device__ __forceinline__ bool tab2_ok(int W, int H, int r)
 {
-    const int j = slot >> 1;
-    const int a = (int)((uint32_t)pb.perm[2 * j] ^ xs);
-    const int b = (int)((uint32_t)pb.perm[2 * j + 1] ^ xs);
-    p = (slot & 1) ? b : a;
-    partner = (slot & 1) ? a : b;
+    return W > 2 * (8 + r) && H > 2 * (4 + r);
+}
+
+// ---- compile-time stencil of radius 6: offsets with 0 < dx^2 + dy^2 <= 36, by class ----------
+struct Stencil6 {
+    int n = 0, ncls = 0;
+    int dx[169] = {}, dy[169] = {}, cls[169] = {}, d2[32] = {};
+    constexpr Stencil6()
+    {
+        for (int dd = 1; dd <= 36; ++dd) {
+            bool any = false;
+            for (int y = -6; y <= 6; ++y)
+                for (int x = -6; x <= 6; ++x)
+                    if (x * x + y * y == dd) {
+                        dx[n] = x;
+                        dy[n] = y;
+                        cls[n] = ncls;
+                        ++n;
+                        any = true;
+                    }
+            if (any) d2[ncls++] = dd;
+        }
+    }
+};
+constexpr Stencil6 kSt6{};
+constexpr int kCls6 = 18, kOffPerWarp = 28;
+static_assert(kSt6.n == 4 * kOffPerWarp && kSt6.ncls == kCls6, "radius-6 stencil");
+
+// one offset of the radius-6 stencil: the accumulator row of patch pixel p + offset, if that
+// pixel is in the patch and is not the partner, added to its class sum
+template <int O>
+__device__ __forceinline__ void stencil_add(const float *dtc, int plx, int ply, int plane,
+                                            int lane, int (&a)[kCls6])
+{
+    constexpr int dx = kSt6.dx[O], dy = kSt6.dy[O], c = kSt6.cls[O];
+    const int lx = plx + dx, ly = ply + dy;
+    const int q = ly * kPW + lx;
+    const bool in = (unsigned)lx < (unsigned)kPW && (unsigned)ly < (unsigned)kPH && q != plane;
+    // unconditional load; a lane outside the patch reads its own bank (row lane of its column)
+    const float x = dtc[in ? q : lane];
+    a[c] += in ? __float2int_rn(x) : 0;
+}
+template <int Q, int... I>
+__device__ __forceinline__ void stencil_quarter(const float *dtc, int plx, int ply, int plane,
+                                                int lane, int (&a)[kCls6],
+                                                std::integer_sequence<int, I...>)
+{
+    (stencil_add<Q * kOffPerWarp + I>(dtc, plx, ply, plane, lane, a), ...);
+}
+
+// the problem's classes are those of the static stencil (squared distances in order)
+template <int C>
+struct D2Of6 {
+    static constexpr int v = kSt6.d2[C];
+};
+template <int... C>
+__device__ __forceinline__ bool classes_match6(const int32_t *d2, std::integer_sequence<int, C...>)
+{
+    return ((d2[C] == D2Of6<C>::v) && ...);
 }
 
 // row kinds of a producer task
 enum : int { kRowNone = 0, kRowCount = 1, kRowDelta = 2, kRowZero = 3 };
 
-// In place: the raw bytes of one row (64 counts, or 64 partner then 64 own counts) become its
-// 64 f16 in swizzled order.  r7: the row's swizzle phase (row index mod 8).
+// In place: the raw bytes of one row (64 counts, or 64 partner then 64 own counts; raw 16-byte
+// piece i sits in slot i ^ r7 of the row, so that the 8 rows of a swizzle atom touch distinct
+// banks) become its 64 f16, piece j in slot j ^ r7.  r7: the row index mod 8.
 __device__ __forceinline__ void convert_row(int kind, char *row, uint32_t r7)
 {
     if (kind == kRowNone) return;
@@ -217,7 +304,7 @@ __device__ __forceinline__ void convert_row(int kind, char *row, uint32_t r7)
     if (kind == kRowCount) {
         uint4 v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = raw[i];
+        for (int i = 0; i < 4; ++i) v[i] = raw[i ^ r7];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const uint32_t w0 = (j & 1) ? v[j >> 1].z : v[j >> 1].x;
@@ -228,17 +315,15 @@ __device__ __forceinline__ void convert_row(int kind, char *row, uint32_t r7)
     } else if (kind == kRowDelta) {
         uint4 v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = raw[i];
+        for (int i = 0; i < 8; ++i) v[i] = raw[i ^ r7];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const uint4 pa = v[j >> 1], se = v[4 + (j >> 1)];
             const uint32_t p0 = (j & 1) ? pa.z : pa.x, p1 = (j & 1) ? pa.w : pa.y;
             const uint32_t s0 = (j & 1) ? se.z : se.x, s1 = (j & 1) ? se.w : se.y;
-            // signed byte differences (|d| <= 64), offset by 128 to read them unsigned
-            const uint32_t d0 = __vsub4(p0, s0) ^ 0x80808080u;
-            const uint32_t d1 = __vsub4(p1, s1) ^ 0x80808080u;
-            bytes_to_h2(d0, kBiasDelta, out[j].x, out[j].y);
-            bytes_to_h2(d1, kBiasDelta, out[j].z, out[j].w);
+            // (1024 + partner) - (1024 + own) in f16: exact, |difference| <= 64
+            bytes_sub_h2(p0, s0, out[j].x, out[j].y);
+            bytes_sub_h2(p1, s1, out[j].z, out[j].w);
         }
     } else {
 #pragma unroll
@@ -249,11 +334,30 @@ __device__ __forceinline__ void convert_row(int kind, char *row, uint32_t r7)
 }
 
 // ---- producer warps -----------------------------------------------------------------------
+// One continuous pipeline over the stages of all products: the copies of stage g are issued,
+// then stage g - kLook (possibly of the previous product) is converted and published.  Every
+// thread owns the same two row positions of every stage.
+__device__ __forceinline__ void publish(char *smem, uint64_t *full, uint32_t gi, int kind,
+                                        uint32_t roff)
+{
+    convert_row(kind, smem + (gi % kStages) * kStageBytes + roff, (roff >> 7) & 7u);
+    tc::fence_async_smem();
+    mbar_arrive(&full[gi % kStages]);
+}
+
 __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint64_t *empty,
                            volatile int *abort_flag)
 {
-    const int pt = threadIdx.x - kEpiThreads;  // 0 .. kProdThreads - 1
+    // this thread's row of every stage: A rows 0..127, then B rows 0..kNB-1
+    const int row = threadIdx.x - kEpiThreads;
+    const int nrow = row - kTcM;
+    const uint32_t roff = row < kTcM ? (uint32_t)((row >> 3) * 1024 + (row & 7) * 128)
+                                     : (uint32_t)(kAStage + (nrow >> 3) * 1024 + (nrow & 7) * 128);
+    const uint32_t r7 = (roff >> 7) & 7u;
     const uint32_t sbase = tc::saddr(smem);
+    int kh[kLook];  // row kinds of the stages 1 .. kLook back
+#pragma unroll
+    for (int b = 0; b < kLook; ++b) kh[b] = kRowNone;
     uint32_t g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
@@ -263,84 +367,66 @@ __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint6
         const Problem &pb = *d.pb;
         const int nks = pb.row_bytes >> 6;
         const size_t plane = (size_t)pb.P << 7;
-        const int32_t *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
+        const int4 *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
-            // this thread's rows: A rows 0..127 then B rows 0..npad-1
-            int kind[2];
-            const uint8_t *src0[2], *src1[2];
-            uint32_t roff[2];
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int row = pt + t * kProdThreads;
-                kind[t] = kRowNone;
-                src0[t] = src1[t] = nullptr;
-                roff[t] = 0;
-                if (row < kTcM) {
-                    roff[t] = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
-                    const int qx = d.x0 + (row & 15), qy = d.y0 + (row >> 4);
-                    if (qx < pb.W && qy < pb.H) {
-                        kind[t] = kRowCount;
-                        src0[t] = pb.counts + ((size_t)(qy * pb.W + qx) << 7);
-                    } else {
-                        kind[t] = kRowZero;
-                    }
-                } else if (row < kTcM + npad) {
-                    const int n = row - kTcM;
-                    roff[t] = (uint32_t)(kAStage + (n >> 3) * 1024 + (n & 7) * 128);
-                    if (n < nn) {
-                        int p, partner;
-                        slot_pixels(pb, d.xs, list[n0 + n], p, partner);
-                        kind[t] = kRowDelta;
-                        src0[t] = pb.counts + ((size_t)partner << 7);
-                        src1[t] = pb.counts + ((size_t)p << 7);
-                    } else {
-                        kind[t] = kRowZero;
-                    }
+            int kind = kRowNone;
+            const uint8_t *src0 = nullptr, *src1 = nullptr;
+            if (row < kTcM) {
+                const int qx = d.x0 + (row & 15), qy = d.y0 + (row >> 4);
+                if (qx < pb.W && qy < pb.H) {
+                    kind = kRowCount;
+                    src0 = pb.counts + ((size_t)(qy * pb.W + qx) << 7);
+                } else {
+                    kind = kRowZero;
+                }
+            } else if (nrow < npad) {
+                if (nrow < nn) {
+                    const int2 e = *reinterpret_cast<const int2 *>(list + n0 + nrow);
+                    kind = kRowDelta;
+                    src0 = pb.counts + ((size_t)e.y << 7);  // partner
+                    src1 = pb.counts + ((size_t)e.x << 7);  // the proposed pixel
+                } else {
+                    kind = kRowZero;
                 }
             }
-            for (int ks = 0; ks < nks + kLook; ++ks) {
-                if (ks < nks) {
-                    const uint32_t gi = g + (uint32_t)ks;
-                    const uint32_t slot = gi % kStages, use = gi / kStages;
-                    if (!tc_wait(&empty[slot], (use & 1u) ^ 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t st = sbase + slot * kStageBytes;
-                    const size_t off = (size_t)(ks >> 1) * plane + (size_t)(ks & 1) * 64;
+            for (int ks = 0; ks < nks; ++ks) {
+                const uint32_t slot = g % kStages, use = g / kStages;
+                if (!tc_wait(&empty[slot], (use & 1u) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = sbase + slot * kStageBytes + roff;
+                const size_t off = (size_t)(ks >> 1) * plane + (size_t)(ks & 1) * 64;
+                if (kind == kRowCount || kind == kRowDelta) {
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        if (kind[t] == kRowCount || kind[t] == kRowDelta) {
+                    for (int i = 0; i < 4; ++i)
+                        cp_async16(st + ((i ^ r7) << 4), src0 + off + 16 * i);
+                }
+                if (kind == kRowDelta) {
 #pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                cp_async16(st + roff[t] + 16 * i, src0[t] + off + 16 * i);
-                        }
-                        if (kind[t] == kRowDelta) {
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                cp_async16(st + roff[t] + 64 + 16 * i, src1[t] + off + 16 * i);
-                        }
-                    }
+                    for (int i = 0; i < 4; ++i)
+                        cp_async16(st + (((4 + i) ^ r7) << 4), src1 + off + 16 * i);
                 }
                 cp_async_commit();
-                if (ks >= kLook) {
+                if (g >= (uint32_t)kLook) {
                     cp_async_wait<kLook>();
-                    const uint32_t gi = g + (uint32_t)(ks - kLook);
-                    const uint32_t slot = gi % kStages;
-                    char *st = smem + slot * kStageBytes;
-#pragma unroll
-                    for (int t = 0; t < 2; ++t)
-                        convert_row(kind[t], st + roff[t], (roff[t] >> 7) & 7u);
-                    tc::fence_async_smem();
-                    mbar_arrive(&full[slot]);
+                    publish(smem, full, g - kLook, kh[kLook - 1], roff);
                 }
+#pragma unroll
+                for (int b = kLook - 1; b > 0; --b) kh[b] = kh[b - 1];
+                kh[0] = kind;
+                ++g;
             }
-            g += (uint32_t)nks;
         }
     }
     cp_async_wait<0>();
+    if (ok) {  // the last kLook stages, oldest first
+#pragma unroll
+        for (int b = kLook - 1; b >= 0; --b)
+            if (g >= (uint32_t)(b + 1)) publish(smem, full, g - (uint32_t)(b + 1), kh[b], roff);
+    }
 }
 
 // ---- MMA warp -------------------------------------------------------------------------------
@@ -404,8 +490,14 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
     const int et = threadIdx.x;  // 0 .. 127: tensor-memory lane = patch pixel
     const int w = et >> 5;
     int32_t *acc = reinterpret_cast<int32_t *>(smem + kOffAcc);
+    float *dt = reinterpret_cast<float *>(smem + kOffAcc);         // [32][128], column path
+    int32_t *part = reinterpret_cast<int32_t *>(smem + kOffPart);  // [4][32][33], column path
+    // per listed pixel: (table offset, partner, slot, x | y << 16) and, for the column path,
+    // (its patch-local x, y, the partner's patch pixel or -1)
     int4 *col = reinterpret_cast<int4 *>(smem + kOffCol);
+    int4 *col1 = col + kNB;
     int32_t *tab = reinterpret_cast<int32_t *>(smem + kOffTab);
+    int8_t *tab2 = reinterpret_cast<int8_t *>(smem + kOffTab2);
     uint32_t jb = 0;
     int cur = -1;
     bool ok = true;
@@ -413,32 +505,53 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
         int pi;
         const Unit d = decode_unit(args, u, pi);
         const Problem &pb = *d.pb;
-        if (d.cnt > 0 && pi != cur) {  // class of each squared distance of this problem
+        const int W = pb.W, H = pb.H, hw = W >> 1, hh = H >> 1;
+        const int r = pb.radius, r2 = r * r, ncls = pb.n_cls;
+        const bool fast = tab2_ok(W, H, r);
+        const int tw = tab2_w(r);
+        // column-per-thread path: radius 6 with the classes of the static stencil
+        const bool colpath = fast && r == 6 && ncls == kCls6 &&
+                             classes_match6(pb.d2, std::make_integer_sequence<int, kCls6>{});
+        if (d.cnt > 0 && pi != cur) {  // class of each squared distance / offset of this problem
             epi_sync();
             for (int i = et; i < kTabMax; i += kEpiThreads) tab[i] = -1;
             epi_sync();
-            if (et < pb.n_cls) tab[pb.d2[et]] = et;
+            if (et < ncls) tab[pb.d2[et]] = et;
             epi_sync();
+            if (fast) {
+                const int dxm = tab2_dx(r), n2 = tw * (2 * tab2_dy(r) + 1);
+                for (int i = et; i < n2; i += kEpiThreads) {
+                    const int dx = i % tw - dxm, dy = i / tw - tab2_dy(r);
+                    const int dd = dx * dx + dy * dy;
+                    tab2[i] = (int8_t)(dd <= r2 ? tab[dd] : -1);
+                }
+                epi_sync();
+            }
             cur = pi;
         }
-        const int qx = d.x0 + (et & 15), qy = d.y0 + (et >> 4);
-        const bool qin = qx < pb.W && qy < pb.H;
-        const int qpix = qy * pb.W + qx;
-        const int W = pb.W, H = pb.H, hw = pb.W >> 1, hh = pb.H >> 1;
-        const int r2 = pb.radius * pb.radius, ncls = pb.n_cls;
-        const int32_t *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
+        const int lx = et & 15, ly = et >> 4;
+        const int qx = d.x0 + lx, qy = d.y0 + ly;
+        const bool qin = qx < W && qy < H;
+        const int qpix = qy * W + qx;
+        // this lane's part of the 2-D table index (offsets from the patch centre)
+        const int lt = (ly - kPH / 2 + tab2_dy(r)) * tw + (lx - kPW / 2 + tab2_dx(r));
+        int32_t *const side = pb.side_cls;
+        const int4 *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
         for (int n0 = 0; n0 < d.cnt; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
             const uint32_t buf = jb & 1u;
             for (int n = et; n < nn; n += kEpiThreads) {
-                const int slot = list[n0 + n];
-                int p, partner;
-                slot_pixels(pb, d.xs, slot, p, partner);
-                col[n] = make_int4(p % W, p / W, partner, slot);
+                const int4 e = list[n0 + n];
+                const int rx = (int)(int16_t)(e.w & 0xFFFF), ry = e.w >> 16;
+                col[n] = make_int4(ry * tw + rx, e.y, e.z, (e.x % W) | ((e.x / W) << 16));
+                const int ax = e.y % W - d.x0, ay = e.y / W - d.y0;
+                const int plane = (ax >= 0 && ax < kPW && ay >= 0 && ay < kPH) ? ay * kPW + ax : -1;
+                col1[n] = make_int4(rx + kPW / 2, ry + kPH / 2, plane, 0);
             }
-            for (int e = et; e < nn * 8; e += kEpiThreads)
-                reinterpret_cast<int4 *>(acc)[e] = make_int4(0, 0, 0, 0);
+            if (!colpath)
+                for (int e = et; e < nn * 8; e += kEpiThreads)
+                    reinterpret_cast<int4 *>(acc)[e] = make_int4(0, 0, 0, 0);
             epi_sync();
             const bool wok = tc_wait(&tfull[buf], (jb >> 1) & 1u, abort_flag);
             if (epi_any(!wok)) {
@@ -450,13 +563,67 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
                 uint32_t v[32];
                 tc::tmem_ld32(tmem + buf * kTmemBuf + (uint32_t)c0 + ((uint32_t)(w * 32) << 16),
                               v);
-                if (qin) {
+                if (colpath) {
+                    // transpose 32 columns through shared memory; warp w then sums, for the
+                    // column of each lane, its quarter of the 112 stencil offsets
+                    const int lane = et & 31;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) dt[i * kTcM + et] = __uint_as_float(v[i]);
+                    epi_sync();
+                    int a[kCls6];
+#pragma unroll
+                    for (int c = 0; c < kCls6; ++c) a[c] = 0;
+                    if (c0 + lane < nn) {
+                        const int4 c1 = col1[c0 + lane];
+                        const float *dtc = dt + lane * kTcM;
+                        using Seq = std::make_integer_sequence<int, kOffPerWarp>;
+                        switch (w) {
+                        case 0: stencil_quarter<0>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+                        case 1: stencil_quarter<1>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+                        case 2: stencil_quarter<2>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+                        default: stencil_quarter<3>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < kCls6; ++c) part[(w * 32 + lane) * 33 + c] = a[c];
+                    epi_sync();
+                    // sums of the four quarters: warp w takes columns w, w + 4, ...; lane = class
+                    for (int cl = w; cl < 32; cl += 4) {
+                        const int n = c0 + cl;
+                        if (n < nn && lane < kCls6) {
+                            const int sum = part[cl * 33 + lane] + part[(32 + cl) * 33 + lane] +
+                                            part[(64 + cl) * 33 + lane] +
+                                            part[(96 + cl) * 33 + lane];
+                            if (sum)
+                                red_add_global(side + (size_t)col[n].z * kMaxClasses + lane, sum);
+                        }
+                    }
+                } else if (qin && fast) {
+                    // per 16 columns: the table lookups first (independent loads), then the
+                    // class-sum updates
+#pragma unroll
+                    for (int h = 0; h < 32; h += 16) {
+                        int cls[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int n = c0 + h + i < nn ? c0 + h + i : nn - 1;
+                            const int2 ci = *reinterpret_cast<const int2 *>(col + n);
+                            const int c = tab2[lt - ci.x];
+                            cls[i] = (c0 + h + i < nn && qpix != ci.y) ? c : -1;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (cls[i] >= 0)
+                                atomicAdd(&acc[(c0 + h + i) * 32 + cls[i]],
+                                          __float2int_rn(__uint_as_float(v[h + i])));
+                    }
+                } else if (qin) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int n = c0 + i;
                         if (n < nn) {
                             const int4 ci = col[n];
-                            int dx = qx - ci.x, dy = qy - ci.y;
+                            int dx = qx - (ci.w & 0xFFFF), dy = qy - (ci.w >> 16);
                             dx += dx < -hw ? W : 0;
                             dx -= dx > hw ? W : 0;
                             dy += dy < -hh ? H : 0;
@@ -464,7 +631,7 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
                             const int d2 = dx * dx + dy * dy;  // |dx| <= W/2, |dy| <= H/2
                             if (d2 <= r2) {
                                 const int c = tab[d2];  // -1 for d2 = 0 and empty classes
-                                if (c >= 0 && qpix != ci.z)
+                                if (c >= 0 && qpix != ci.y)
                                     atomicAdd(&acc[n * 32 + c],
                                               __float2int_rn(__uint_as_float(v[i])));
                             }
@@ -475,11 +642,20 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
             tc::fence_before_sync();
             mbar_arrive(&tempty[buf]);
             epi_sync();
-            for (int e = et; e < nn * 32; e += kEpiThreads) {
-                const int c = e & 31;
-                if (c < ncls) {
-                    const int val = acc[e];
-                    if (val) atomicAdd(pb.side_cls + (size_t)col[e >> 5].w * kMaxClasses + c, val);
+            // warp w sends the class sums of columns w, w + 4, ...; lane = class
+            if (!colpath) {
+                const int lane = et & 31;
+                for (int nb = w; nb < nn; nb += 4 * kFlushBatch) {
+                    int val[kFlushBatch], slot[kFlushBatch];
+#pragma unroll
+                    for (int k = 0; k < kFlushBatch; ++k) {
+                        const int n = nb + 4 * k;
+                        val[k] = (n < nn && lane < ncls) ? acc[n * 32 + lane] : 0;
+                        slot[k] = n < nn ? col[n].z : 0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kFlushBatch; ++k)
+                        if (val[k]) red_add_global(side + (size_t)slot[k] * kMaxClasses + lane, val[k]);
                 }
             }
             epi_sync();
@@ -589,7 +765,15 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
                 if (xd[u] * xd[u] + yd[v] * yd[v] > r2) continue;  // patch out of reach
                 const int pid = yi[v] * pb.tc_npx + xi[u];
                 const int pos = atomicAdd(pb.tc_cnt + pid, 1);
-                if (pos < pb.tc_cap) pb.tc_list[(size_t)pid * pb.tc_cap + pos] = 2 * j + side;
+                // min-image offset of p from the patch centre -> fast-path table offset
+                int rx = px - (xi[u] * kPW + kPW / 2), ry = py - (yi[v] * kPH + kPH / 2);
+                rx -= rx > (pb.W >> 1) ? pb.W : 0;
+                rx += rx < -(pb.W >> 1) ? pb.W : 0;
+                ry -= ry > (pb.H >> 1) ? pb.H : 0;
+                ry += ry < -(pb.H >> 1) ? pb.H : 0;
+                if (pos < pb.tc_cap)
+                    pb.tc_list[(size_t)pid * pb.tc_cap + pos] =
+                        make_int4(p, side ? a : b, 2 * j + side, (rx & 0xFFFF) | (ry << 16));
             }
     }
 }
