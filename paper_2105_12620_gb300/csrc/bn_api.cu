@@ -107,6 +107,11 @@ struct SweepPlan {
     bool tensor = false;            // tensor-core schedule (every problem has 8-bit counts)
     int *d_tc_prefix = nullptr;     // [n_prob + 1] prefix sums of 16 x 8 patches
     int tc_units = 0;
+    // the problems as the tensor-core kernels see them: the same state plus the plan's f16
+    // count copies and per-pass delta rows (allocations in tc_bufs)
+    bn::Problem *d_tcprob = nullptr;
+    std::vector<bn::Problem> tcprob;
+    std::vector<void *> tc_bufs;
     bn::PersistentShape shape{8, 8, 256, 4, 0};
     // per count width (index cb - 1): first problem, problem count, units / couples prefix
     int first[2] = {0, 0}, count[2] = {0, 0};
@@ -138,6 +143,11 @@ void free_plan(SweepPlan &pl)
     if (pl.d_tmaps) cudaFree(pl.d_tmaps);
     if (pl.d_tc_prefix) cudaFree(pl.d_tc_prefix);
     pl.d_tc_prefix = nullptr;
+    if (pl.d_tcprob) cudaFree(pl.d_tcprob);
+    pl.d_tcprob = nullptr;
+    for (void *b : pl.tc_bufs) cudaFree(b);
+    pl.tc_bufs.clear();
+    pl.tcprob.clear();
     pl.tensor = false;
     pl.persistent = false;
     pl.tc_units = 0;
@@ -400,6 +410,19 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
         for (int i = 0; i < pl.n_prob; ++i) pre[i + 1] = pre[i] + bn::tc_units_per_problem(hp[i]);
         pl.tc_units = pre[pl.n_prob];
         BN_CUDA(bn::prepare_tc());
+        pl.tcprob = hp;
+        for (auto &h : pl.tcprob) {
+            void *m = nullptr, *d = nullptr;
+            BN_CUDA(cudaMalloc(&m, (size_t)h.P * h.row_bytes * 2));
+            pl.tc_bufs.push_back(m);
+            BN_CUDA(cudaMalloc(&d, (size_t)h.M * h.row_bytes * 2));
+            pl.tc_bufs.push_back(d);
+            h.tc_counts16 = static_cast<uint16_t *>(m);
+            h.tc_delta16 = static_cast<uint16_t *>(d);
+        }
+        BN_CUDA(cudaMalloc(&pl.d_tcprob, sizeof(bn::Problem) * pl.tcprob.size()));
+        BN_CUDA(cudaMemcpy(pl.d_tcprob, pl.tcprob.data(), sizeof(bn::Problem) * pl.tcprob.size(),
+                           cudaMemcpyHostToDevice));
         BN_CUDA(cudaMalloc(&pl.d_tc_prefix, sizeof(int) * pre.size()));
         BN_CUDA(cudaMemcpy(pl.d_tc_prefix, pre.data(), sizeof(int) * pre.size(),
                            cudaMemcpyHostToDevice));
@@ -512,11 +535,12 @@ cudaError_t launch_pass(const SweepPlan &pl, const bn::SweepLaunch &sl, cudaStre
                         bn::KernelTimer *tm)
 {
     if (!pl.tensor) return bn::launch_plain_sweep(sl, st, tm);
-    const bn::TcLaunch tl{sl.dprob, sl.n_prob, pl.max_M, pl.d_tc_prefix, pl.tc_units, pl.sms};
+    const bn::TcLaunch tl{pl.d_tcprob, sl.n_prob, pl.max_M, pl.d_tc_prefix, pl.tc_units, pl.sms};
     return bn::launch_tc_sweep(tl, st, tm);
 }
 
-int launches_per_pass(const SweepPlan &pl) { return pl.tensor ? 5 : 3; }
+int launches_per_pass(const SweepPlan &pl) { return pl.tensor ? 5 : 3; }  // lists+deltas, stencil,
+                                                                           // finalize, resolve, commit
 
 // Capture graph_passes passes of the plain or tensor-core schedule as one CUDA graph.  Every
 // kernel reads the pass index and budget from device memory, so the graph replays.
@@ -546,6 +570,8 @@ int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Prob
              int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm, bool set_end = true)
 {
     if (set_end) BN_CUDA(bn::launch_set_end(dprob, pl.n_prob, n_sweeps, 1, st));
+    if (pl.tensor && n_sweeps > 0)  // the f16 count copies follow whatever ran since
+        BN_CUDA(bn::launch_tc_refresh(pl.d_tcprob, pl.tcprob, st));
     if (!pl.persistent) {
         // per-kernel timing needs the individual launches
         const bool graphs = pl.graph_passes > 0 && !(tm && tm->enabled);

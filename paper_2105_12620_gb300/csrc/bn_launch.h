@@ -48,7 +48,7 @@ cudaError_t launch_energy_copy(const Problem *dprob, int n_prob, double *dev_out
 
 // Optional CUDA-event bracketing of kernel launches (host side).
 enum KernelKind { kKEvalPlain = 0, kKResolvePlain, kKCommitPlain, kKPersistent, kKEnergy,
-                  kKCounts, kKTcStencil, kKindCount };
+                  kKCounts, kKTcStencil, kKTcLists, kKTcFinalize, kKindCount };
 extern const char *const kKernelNames[kKindCount];
 
 struct KernelTimer {
@@ -78,7 +78,7 @@ struct SweepLaunch {
 };
 cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm);
 // resolve + commit of the plain schedule alone
-cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st);
+cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm);
 cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int reset_stats,
                            cudaStream_t st);
 cudaError_t launch_set_ends(const Problem *dprob, int n_prob, const int *n_sweeps_dev,
@@ -97,5 +97,8 @@ bool tc_supported(const Problem &h);
 int tc_units_per_problem(const Problem &h);
 cudaError_t prepare_tc();
 cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm);
+// f16 copies of the counts (tc_counts16) from the counts, every problem
+cudaError_t launch_tc_refresh(const Problem *dprob, const std::vector<Problem> &hp,
+                              cudaStream_t st);
 
 }  // namespace bn

@@ -168,6 +168,19 @@ __global__ void __launch_bounds__(kPlainThreads) k_commit_plain(const Problem *p
                 *ra = *rb;
                 *rb = t;
             }
+            if (pb.tc_counts16) {  // the f16 copy of the tensor-core schedule
+                const int nv = pb.row_bytes >> 3;  // 16-byte pieces of f16 per pixel
+                for (int vi = lane; vi < nv; vi += 32) {
+                    const size_t plane = (size_t)(vi >> 3) * pb.P;
+                    uint4 *ra = reinterpret_cast<uint4 *>(pb.tc_counts16 + ((plane + a) << 6)) +
+                                (vi & 7);
+                    uint4 *rb = reinterpret_cast<uint4 *>(pb.tc_counts16 + ((plane + b) << 6)) +
+                                (vi & 7);
+                    const uint4 t = *ra;
+                    *ra = *rb;
+                    *rb = t;
+                }
+            }
             if (lane == 0) {
                 const int t = pb.sidx[a];
                 pb.sidx[a] = pb.sidx[b];
@@ -252,11 +265,16 @@ cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTim
 }
 
 // the resolve and commit kernels alone (the tensor-core schedule evaluates couples itself)
-cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st)
+cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm)
 {
+    const bool timed = tm && tm->enabled;
     dim3 grid((sl.max_M + kPlainWarps - 1) / kPlainWarps, sl.n_prob);
+    if (timed) tm->begin(kKResolvePlain, st);
     k_resolve_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
+    if (timed) tm->end(st);
+    if (timed) tm->begin(kKCommitPlain, st);
     k_commit_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
+    if (timed) tm->end(st);
     note_launches(2);
     return cudaGetLastError();
 }
@@ -265,7 +283,8 @@ cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st)
 const char *const kKernelNames[kKindCount] = {"eval_plain",       "resolve_plain",
                                                "commit_plain",     "sweep_persistent",
                                                "energy",           "counts",
-                                               "stencil_tensor"};
+                                               "stencil_tensor",   "lists_tensor",
+                                               "finalize_tensor"};
 
 cudaEvent_t KernelTimer::get()
 {

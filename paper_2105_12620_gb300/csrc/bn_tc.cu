@@ -17,10 +17,10 @@
 //   k_tc_lists     couples of the pass as in the plain schedule; each proposed pixel is appended
 //                  to the list of every patch within the radius of it; its class sums cleared
 //   k_tc_stencil   one CTA per SM over the patches, warp-specialised:
-//                    9 producer warps   count bytes -> shared memory (cp.async), converted in
-//                                       place to f16 in the 128-byte swizzled K-major layout,
-//                                       deltas formed on the way; one row of every stage per
-//                                       thread; stages of 64 integrands
+//                    9 producer warps   count bytes -> shared memory (cp.async, eight whole
+//                                       rows per warp instruction), converted in place to f16
+//                                       in the 128-byte swizzled K-major layout, deltas formed
+//                                       on the way; stages of 64 integrands
 //                    1 MMA warp         four tcgen05.mma (K = 16 each) per stage
 //                    4 epilogue warps   tensor memory -> registers; entries inside the radius
 //                                       go to per-pixel class sums in shared memory, then to
@@ -45,7 +45,7 @@ constexpr int kLook = 3;                             // stages in flight per pro
 constexpr int kAStage = kTcM * 128;                  // 16 KB: 128 rows x 64 f16
 constexpr int kBStage = kNB * 128;                   // 20 KB: 160 rows x 64 f16
 constexpr int kStageBytes = kAStage + kBStage;
-constexpr int kEpiWarps = 4, kProdWarps = (kTcM + kNB) / 32;  // one producer thread per row
+constexpr int kEpiWarps = 4, kProdWarps = (kTcM + kNB) / 32;  // four pieces per thread
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void stencil_add(const float *dtc, int plx, int ply, 
     const bool in = (unsigned)lx < (unsigned)kPW && (unsigned)ly < (unsigned)kPH && q != plane;
     // unconditional load; a lane outside the patch reads its own bank (row lane of its column)
     const float x = dtc[in ? q : lane];
-    a[c] += in ? __float2int_rn(x) : 0;
+    a[c] += in ? __float2int_rn(x) : 0;  // an exact integer held in f32
 }
 template <int Q, int... I>
 __device__ __forceinline__ void stencil_quarter(const float *dtc, int plx, int ply, int plane,
@@ -277,6 +277,18 @@ __device__ __forceinline__ void stencil_quarter(const float *dtc, int plx, int p
                                                 std::integer_sequence<int, I...>)
 {
     (stencil_add<Q * kOffPerWarp + I>(dtc, plx, ply, plane, lane, a), ...);
+}
+// warp w's quarter of the stencil offsets
+__device__ __forceinline__ void stencil_warp(int w, const float *dtc, int4 c1, int lane,
+                                             int (&a)[kCls6])
+{
+    using Seq = std::make_integer_sequence<int, kOffPerWarp>;
+    switch (w) {
+    case 0: stencil_quarter<0>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+    case 1: stencil_quarter<1>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+    case 2: stencil_quarter<2>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+    default: stencil_quarter<3>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+    }
 }
 
 // the problem's classes are those of the static stencil (squared distances in order)
@@ -290,74 +302,52 @@ __device__ __forceinline__ bool classes_match6(const int32_t *d2, std::integer_s
     return ((d2[C] == D2Of6<C>::v) && ...);
 }
 
+// ---- producer warps -----------------------------------------------------------------------
+// A stage holds 128 A rows (the patch pixels' f16 counts) and up to kNB B rows (the listed
+// couples' f16 deltas) of 64 integrands, each row eight 16-byte pieces, copied by cp.async
+// straight into the swizzled slots (piece j of row r in slot j ^ (r mod 8)).  Producer thread pt
+// owns the pieces pt + kProdThreads k, k < kTasks: a warp copies four whole 128-byte rows per
+// instruction.  A rows of pixels outside a ragged tile are written as zeros.
+constexpr int kTasks = 8;
+static_assert(kTasks * kProdThreads == 8 * (kTcM + kNB), "one piece per task");
+static_assert(kProdThreads % 8 == 0, "the piece index is the same for all of a thread's tasks");
+
 // row kinds of a producer task
 enum : int { kRowNone = 0, kRowCount = 1, kRowDelta = 2, kRowZero = 3 };
 
-// In place: the raw bytes of one row (64 counts, or 64 partner then 64 own counts; raw 16-byte
-// piece i sits in slot i ^ r7 of the row, so that the 8 rows of a swizzle atom touch distinct
-// banks) become its 64 f16, piece j in slot j ^ r7.  r7: the row index mod 8.
-__device__ __forceinline__ void convert_row(int kind, char *row, uint32_t r7)
+// make this thread's copies (and zero stores) of stage gi visible to the tensor core, then one
+// arrival per warp
+__device__ __forceinline__ void publish(char *smem, uint64_t *full, uint32_t gi, uint32_t kinds,
+                                        const uint32_t (&roff)[kTasks], int piece)
 {
-    if (kind == kRowNone) return;
-    uint4 out[8];
-    uint4 *raw = reinterpret_cast<uint4 *>(row);
-    if (kind == kRowCount) {
-        uint4 v[4];
+    char *st = smem + (gi % kStages) * kStageBytes;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = raw[i ^ r7];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t w0 = (j & 1) ? v[j >> 1].z : v[j >> 1].x;
-            const uint32_t w1 = (j & 1) ? v[j >> 1].w : v[j >> 1].y;
-            bytes_to_h2(w0, kBiasCount, out[j].x, out[j].y);
-            bytes_to_h2(w1, kBiasCount, out[j].z, out[j].w);
-        }
-    } else if (kind == kRowDelta) {
-        uint4 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = raw[i ^ r7];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint4 pa = v[j >> 1], se = v[4 + (j >> 1)];
-            const uint32_t p0 = (j & 1) ? pa.z : pa.x, p1 = (j & 1) ? pa.w : pa.y;
-            const uint32_t s0 = (j & 1) ? se.z : se.x, s1 = (j & 1) ? se.w : se.y;
-            // (1024 + partner) - (1024 + own) in f16: exact, |difference| <= 64
-            bytes_sub_h2(p0, s0, out[j].x, out[j].y);
-            bytes_sub_h2(p1, s1, out[j].z, out[j].w);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) out[j] = make_uint4(0u, 0u, 0u, 0u);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) raw[j ^ r7] = out[j];
-}
-
-// ---- producer warps -----------------------------------------------------------------------
-// One continuous pipeline over the stages of all products: the copies of stage g are issued,
-// then stage g - kLook (possibly of the previous product) is converted and published.  Every
-// thread owns the same two row positions of every stage.
-__device__ __forceinline__ void publish(char *smem, uint64_t *full, uint32_t gi, int kind,
-                                        uint32_t roff)
-{
-    convert_row(kind, smem + (gi % kStages) * kStageBytes + roff, (roff >> 7) & 7u);
+    for (int k = 0; k < kTasks; ++k)
+        if (((kinds >> (2 * k)) & 3u) == (uint32_t)kRowZero)
+            reinterpret_cast<uint4 *>(st + roff[k])[piece ^ ((roff[k] >> 7) & 7u)] =
+                make_uint4(0u, 0u, 0u, 0u);
     tc::fence_async_smem();
-    mbar_arrive(&full[gi % kStages]);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&full[gi % kStages]);
 }
 
 __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint64_t *empty,
                            volatile int *abort_flag)
 {
-    // this thread's row of every stage: A rows 0..127, then B rows 0..kNB-1
-    const int row = threadIdx.x - kEpiThreads;
-    const int nrow = row - kTcM;
-    const uint32_t roff = row < kTcM ? (uint32_t)((row >> 3) * 1024 + (row & 7) * 128)
-                                     : (uint32_t)(kAStage + (nrow >> 3) * 1024 + (nrow & 7) * 128);
-    const uint32_t r7 = (roff >> 7) & 7u;
-    const uint32_t sbase = tc::saddr(smem);
-    int kh[kLook];  // row kinds of the stages 1 .. kLook back
+    const int pt = threadIdx.x - kEpiThreads;
+    const int piece = pt & 7;
+    constexpr int kRowStep = kProdThreads / 8;  // rows between a thread's tasks
+    uint32_t roff[kTasks];
 #pragma unroll
-    for (int b = 0; b < kLook; ++b) kh[b] = kRowNone;
+    for (int k = 0; k < kTasks; ++k) {
+        const int row = (pt >> 3) + kRowStep * k, n = row - kTcM;
+        roff[k] = row < kTcM ? (uint32_t)((row >> 3) * 1024 + (row & 7) * 128)
+                             : (uint32_t)(kAStage + (n >> 3) * 1024 + (n & 7) * 128);
+    }
+    const uint32_t sbase = tc::saddr(smem);
+    uint32_t kh[kLook];  // packed task kinds of the stages 1 .. kLook back
+#pragma unroll
+    for (int b = 0; b < kLook; ++b) kh[b] = 0u;
     uint32_t g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
@@ -366,30 +356,32 @@ __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint6
         if (d.cnt <= 0) continue;
         const Problem &pb = *d.pb;
         const int nks = pb.row_bytes >> 6;
-        const size_t plane = (size_t)pb.P << 7;
+        const uint16_t *const cnt16 = pb.tc_counts16 + 8 * piece;
+        const uint16_t *const del16 = pb.tc_delta16 + 8 * piece;
+        const size_t cplane = (size_t)pb.P << 6, dplane = (size_t)pb.M << 6;  // f16 per stage
         const int4 *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
-            const int npad = (nn + 15) & ~15;
-            int kind = kRowNone;
-            const uint8_t *src0 = nullptr, *src1 = nullptr;
-            if (row < kTcM) {
-                const int qx = d.x0 + (row & 15), qy = d.y0 + (row >> 4);
-                if (qx < pb.W && qy < pb.H) {
-                    kind = kRowCount;
-                    src0 = pb.counts + ((size_t)(qy * pb.W + qx) << 7);
-                } else {
-                    kind = kRowZero;
-                }
-            } else if (nrow < npad) {
-                if (nrow < nn) {
-                    const int2 e = *reinterpret_cast<const int2 *>(list + n0 + nrow);
+            uint32_t kinds = 0u;
+            int idx[kTasks];  // pixel (A) or couple (B) of each task
+#pragma unroll
+            for (int k = 0; k < kTasks; ++k) {
+                int kind = kRowNone;
+                idx[k] = 0;
+                const int row = (pt >> 3) + kRowStep * k;
+                if (row < kTcM) {
+                    const int qx = d.x0 + (row & 15), qy = d.y0 + (row >> 4);
+                    if (qx < pb.W && qy < pb.H) {
+                        kind = kRowCount;
+                        idx[k] = qy * pb.W + qx;
+                    } else {
+                        kind = kRowZero;
+                    }
+                } else if (row - kTcM < nn) {  // rows nn .. npad - 1 feed ignored columns
                     kind = kRowDelta;
-                    src0 = pb.counts + ((size_t)e.y << 7);  // partner
-                    src1 = pb.counts + ((size_t)e.x << 7);  // the proposed pixel
-                } else {
-                    kind = kRowZero;
+                    idx[k] = list[n0 + row - kTcM].z >> 1;  // couple of the listed slot
                 }
+                kinds |= (uint32_t)kind << (2 * k);
             }
             for (int ks = 0; ks < nks; ++ks) {
                 const uint32_t slot = g % kStages, use = g / kStages;
@@ -397,26 +389,24 @@ __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint6
                     ok = false;
                     break;
                 }
-                const uint32_t st = sbase + slot * kStageBytes + roff;
-                const size_t off = (size_t)(ks >> 1) * plane + (size_t)(ks & 1) * 64;
-                if (kind == kRowCount || kind == kRowDelta) {
+                const uint32_t st = sbase + slot * kStageBytes;
+                const uint16_t *ca = cnt16 + (size_t)ks * cplane;
+                const uint16_t *cd = del16 + (size_t)ks * dplane;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        cp_async16(st + ((i ^ r7) << 4), src0 + off + 16 * i);
-                }
-                if (kind == kRowDelta) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        cp_async16(st + (((4 + i) ^ r7) << 4), src1 + off + 16 * i);
+                for (int k = 0; k < kTasks; ++k) {
+                    const uint32_t kind = (kinds >> (2 * k)) & 3u;
+                    const uint32_t dst = st + roff[k] + ((piece ^ ((roff[k] >> 7) & 7u)) << 4);
+                    if (kind == (uint32_t)kRowCount) cp_async16(dst, ca + ((size_t)idx[k] << 6));
+                    if (kind == (uint32_t)kRowDelta) cp_async16(dst, cd + ((size_t)idx[k] << 6));
                 }
                 cp_async_commit();
                 if (g >= (uint32_t)kLook) {
                     cp_async_wait<kLook>();
-                    publish(smem, full, g - kLook, kh[kLook - 1], roff);
+                    publish(smem, full, g - kLook, kh[kLook - 1], roff, piece);
                 }
 #pragma unroll
                 for (int b = kLook - 1; b > 0; --b) kh[b] = kh[b - 1];
-                kh[0] = kind;
+                kh[0] = kinds;
                 ++g;
             }
         }
@@ -425,7 +415,8 @@ __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint6
     if (ok) {  // the last kLook stages, oldest first
 #pragma unroll
         for (int b = kLook - 1; b >= 0; --b)
-            if (g >= (uint32_t)(b + 1)) publish(smem, full, g - (uint32_t)(b + 1), kh[b], roff);
+            if (g >= (uint32_t)(b + 1))
+                publish(smem, full, g - (uint32_t)(b + 1), kh[b], roff, piece);
     }
 }
 
@@ -576,13 +567,7 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
                     if (c0 + lane < nn) {
                         const int4 c1 = col1[c0 + lane];
                         const float *dtc = dt + lane * kTcM;
-                        using Seq = std::make_integer_sequence<int, kOffPerWarp>;
-                        switch (w) {
-                        case 0: stencil_quarter<0>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-                        case 1: stencil_quarter<1>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-                        case 2: stencil_quarter<2>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-                        default: stencil_quarter<3>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-                        }
+                        stencil_warp(w, dtc, c1, lane, a);
                     }
 #pragma unroll
                     for (int c = 0; c < kCls6; ++c) part[(w * 32 + lane) * 33 + c] = a[c];
@@ -594,8 +579,10 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
                             const int sum = part[cl * 33 + lane] + part[(32 + cl) * 33 + lane] +
                                             part[(64 + cl) * 33 + lane] +
                                             part[(96 + cl) * 33 + lane];
+                            const int slot = col[n].z;  // the b side carries -delta
                             if (sum)
-                                red_add_global(side + (size_t)col[n].z * kMaxClasses + lane, sum);
+                                red_add_global(side + (size_t)slot * kMaxClasses + lane,
+                                               (slot & 1) ? -sum : sum);
                         }
                     }
                 } else if (qin && fast) {
@@ -650,8 +637,9 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
 #pragma unroll
                     for (int k = 0; k < kFlushBatch; ++k) {
                         const int n = nb + 4 * k;
-                        val[k] = (n < nn && lane < ncls) ? acc[n * 32 + lane] : 0;
                         slot[k] = n < nn ? col[n].z : 0;
+                        val[k] = (n < nn && lane < ncls) ? acc[n * 32 + lane] : 0;
+                        if (slot[k] & 1) val[k] = -val[k];  // the b side carries -delta
                     }
 #pragma unroll
                     for (int k = 0; k < kFlushBatch; ++k)
@@ -679,7 +667,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
-            mbar_init(&full[i], kProdThreads);
+            mbar_init(&full[i], kProdWarps);
             mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -734,47 +722,87 @@ __device__ __forceinline__ void note_patch(int (&idx)[kMaxMet], int (&dist)[kMax
     }
 }
 
+// One warp per couple: the couple's class sums are cleared, its f16 delta row k_b - k_a is
+// written for every stage, and each of its two pixels is appended to the lists of the patches
+// within the radius of it (lane 0: pixel a, lane 1: pixel b).
 __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
 {
     const Problem &pb = probs[blockIdx.y];
     const long long s = pb.ctr[0];
     if (s >= pb.ctr[1]) return;
-    const int j = blockIdx.x * kListThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (kListThreads / 32) + (threadIdx.x >> 5);
     if (j >= pb.M) return;
     const uint32_t xs = pass_xor(pb, (uint32_t)s);
     const int a = (int)((uint32_t)pb.perm[2 * j] ^ xs);
     const int b = (int)((uint32_t)pb.perm[2 * j + 1] ^ xs);
     if (a >= pb.P || b >= pb.P) return;
-    int4 *cls = reinterpret_cast<int4 *>(pb.side_cls + (size_t)j * 2 * kMaxClasses);
-#pragma unroll
-    for (int i = 0; i < 2 * kMaxClasses / 4; ++i) cls[i] = make_int4(0, 0, 0, 0);
+    if (lane < 2 * kMaxClasses / 4)
+        reinterpret_cast<int4 *>(pb.side_cls + (size_t)j * 2 * kMaxClasses)[lane] =
+            make_int4(0, 0, 0, 0);
+    // deltas: piece v = 8 integrands of stage v / 8
+    const int nv = (pb.row_bytes >> 6) * 8;
+    for (int v = lane; v < nv; v += 32) {
+        const int e0 = v * 8;  // first integrand of the piece
+        const size_t cb = ((size_t)(e0 >> 7) * pb.P) << 7;
+        const uint2 ka = *reinterpret_cast<const uint2 *>(pb.counts + cb + ((size_t)a << 7) +
+                                                          (e0 & 127));
+        const uint2 kb = *reinterpret_cast<const uint2 *>(pb.counts + cb + ((size_t)b << 7) +
+                                                          (e0 & 127));
+        uint4 o;
+        bytes_sub_h2(kb.x, ka.x, o.x, o.y);
+        bytes_sub_h2(kb.y, ka.y, o.z, o.w);
+        *reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(v >> 3) * pb.M + j) << 6) +
+                                   (v & 7) * 8) = o;
+    }
+    if (lane >= 2) return;
+    const int side = lane;
     const int r = pb.radius, r2 = r * r;
-    for (int side = 0; side < 2; ++side) {
-        const int p = side ? b : a, px = p % pb.W, py = p / pb.W;
-        // distinct patch columns (rows) met by x in [px - r, px + r] (y likewise), torus-wrapped,
-        // with the smallest |offset| that reaches each (a walk can leave a patch and come back
-        // to it on a narrow torus, so every earlier entry is checked)
-        int xi[kMaxMet], xd[kMaxMet], yi[kMaxMet], yd[kMaxMet], nx = 0, ny = 0;
-        for (int dd = -r; dd <= r; ++dd) {
-            const int ad = dd < 0 ? -dd : dd;
-            note_patch(xi, xd, nx, wrap_add(px, dd, pb.W) / kPW, ad);
-            note_patch(yi, yd, ny, wrap_add(py, dd, pb.H) / kPH, ad);
+    const int p = side ? b : a, px = p % pb.W, py = p / pb.W;
+    // distinct patch columns (rows) met by x in [px - r, px + r] (y likewise), torus-wrapped,
+    // with the smallest |offset| that reaches each (a walk can leave a patch and come back
+    // to it on a narrow torus, so every earlier entry is checked)
+    int xi[kMaxMet], xd[kMaxMet], yi[kMaxMet], yd[kMaxMet], nx = 0, ny = 0;
+    for (int dd = -r; dd <= r; ++dd) {
+        const int ad = dd < 0 ? -dd : dd;
+        note_patch(xi, xd, nx, wrap_add(px, dd, pb.W) / kPW, ad);
+        note_patch(yi, yd, ny, wrap_add(py, dd, pb.H) / kPH, ad);
+    }
+    for (int u = 0; u < nx; ++u)
+        for (int w = 0; w < ny; ++w) {
+            if (xd[u] * xd[u] + yd[w] * yd[w] > r2) continue;  // patch out of reach
+            const int pid = yi[w] * pb.tc_npx + xi[u];
+            const int pos = atomicAdd(pb.tc_cnt + pid, 1);
+            // min-image offset of p from the patch centre
+            int rx = px - (xi[u] * kPW + kPW / 2), ry = py - (yi[w] * kPH + kPH / 2);
+            rx -= rx > (pb.W >> 1) ? pb.W : 0;
+            rx += rx < -(pb.W >> 1) ? pb.W : 0;
+            ry -= ry > (pb.H >> 1) ? pb.H : 0;
+            ry += ry < -(pb.H >> 1) ? pb.H : 0;
+            if (pos < pb.tc_cap)
+                pb.tc_list[(size_t)pid * pb.tc_cap + pos] =
+                    make_int4(p, side ? a : b, 2 * j + side, (rx & 0xFFFF) | (ry << 16));
         }
-        for (int u = 0; u < nx; ++u)
-            for (int v = 0; v < ny; ++v) {
-                if (xd[u] * xd[u] + yd[v] * yd[v] > r2) continue;  // patch out of reach
-                const int pid = yi[v] * pb.tc_npx + xi[u];
-                const int pos = atomicAdd(pb.tc_cnt + pid, 1);
-                // min-image offset of p from the patch centre -> fast-path table offset
-                int rx = px - (xi[u] * kPW + kPW / 2), ry = py - (yi[v] * kPH + kPH / 2);
-                rx -= rx > (pb.W >> 1) ? pb.W : 0;
-                rx += rx < -(pb.W >> 1) ? pb.W : 0;
-                ry -= ry > (pb.H >> 1) ? pb.H : 0;
-                ry += ry < -(pb.H >> 1) ? pb.H : 0;
-                if (pos < pb.tc_cap)
-                    pb.tc_list[(size_t)pid * pb.tc_cap + pos] =
-                        make_int4(p, side ? a : b, 2 * j + side, (rx & 0xFFFF) | (ry << 16));
-            }
+}
+
+// f16 copy of the counts: piece v of the copy = 8 integrands of one pixel and stage
+__global__ void k_tc_refresh(const Problem *probs)
+{
+    const Problem &pb = *probs;
+    const long long n = (long long)pb.P * (pb.row_bytes >> 6) * 8;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long per = (long long)pb.P * 8;
+        const int ks = (int)(v / per);
+        const int rem = (int)(v - (long long)ks * per);
+        const int p = rem >> 3, pc = rem & 7;
+        const int e0 = ks * 64 + pc * 8;
+        const uint2 k = *reinterpret_cast<const uint2 *>(
+            pb.counts + ((((size_t)(e0 >> 7) * pb.P) + p) << 7) + (e0 & 127));
+        uint4 o;
+        bytes_to_h2(k.x, kBiasCount, o.x, o.y);
+        bytes_to_h2(k.y, kBiasCount, o.z, o.w);
+        *reinterpret_cast<uint4 *>(pb.tc_counts16 + (((size_t)ks * pb.P + p) << 6) + pc * 8) = o;
     }
 }
 
@@ -834,6 +862,18 @@ bool tc_supported(const Problem &h)
 
 int tc_units_per_problem(const Problem &h) { return h.tc_npx * h.tc_npy; }
 
+cudaError_t launch_tc_refresh(const Problem *dprob, const std::vector<Problem> &hp,
+                              cudaStream_t st)
+{
+    for (size_t i = 0; i < hp.size(); ++i) {
+        const long long n = (long long)hp[i].P * (hp[i].row_bytes >> 6) * 8;
+        const long long blocks = (n + 255) / 256;
+        k_tc_refresh<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(dprob + i);
+    }
+    note_launches((long long)hp.size());
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_tc()
 {
     return cudaFuncSetAttribute(k_tc_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -843,21 +883,26 @@ cudaError_t prepare_tc()
 cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm)
 {
     const dim3 gl((tl.max_M + kListThreads - 1) / kListThreads, tl.n_prob);
-    k_tc_lists<<<gl, kListThreads, 0, st>>>(tl.dprob);
+    const dim3 gw((tl.max_M + kListThreads / 32 - 1) / (kListThreads / 32), tl.n_prob);
+    const bool timed = tm && tm->enabled;
+    if (timed) tm->begin(kKTcLists, st);
+    k_tc_lists<<<gw, kListThreads, 0, st>>>(tl.dprob);
+    if (timed) tm->end(st);
     if (tl.total_units > 0) {
         const TcArgs a{tl.dprob, tl.n_prob, tl.unit_start, tl.total_units};
         const int grid = tl.total_units < tl.sms ? tl.total_units : tl.sms;
-        const bool timed = tm && tm->enabled;
         if (timed) tm->begin(kKTcStencil, st);
         k_tc_stencil<<<grid, kTcThreads, kSmemBytes, st>>>(a);
         if (timed) tm->end(st);
         note_launches(1);
     }
+    if (timed) tm->begin(kKTcFinalize, st);
     k_tc_finalize<<<gl, kListThreads, 0, st>>>(tl.dprob);
+    if (timed) tm->end(st);
     note_launches(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_resolve_commit(SweepLaunch{tl.dprob, tl.n_prob, tl.max_M, 1}, st);
+    return launch_resolve_commit(SweepLaunch{tl.dprob, tl.n_prob, tl.max_M, 1}, st, tm);
 }
 
 }  // namespace bn
