@@ -123,6 +123,25 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
         assert got == value, (name, field, got, value)
 
 
+def test_binding_constants_match_the_header(tmp_path):
+    """Every #define BN_* value of include/bn_sampler.h equals the binding's constant."""
+    import re
+    names = re.findall(r"^#define (BN_(?:OK|ERR_\w+|MODE_\w+|OBJECTIVE_\w+|SCHEDULE_\w+|"
+                       r"INTEGRANDS_\w+))\b", open(L.HEADER).read(), re.M)
+    assert "BN_SCHEDULE_TENSOR" in names
+    src = tmp_path / "consts.c"
+    src.write_text("#include <stdio.h>\n#include \"bn_sampler.h\"\nint main(void) {\n" +
+                   "".join(f'    printf("{n} %d\\n", (int)({n}));\n' for n in names) +
+                   "    return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c99", "-I", L.os.path.dirname(L.HEADER), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        name, value = line.split()
+        assert getattr(L, name) == int(value), name
+
+
 @pytest.mark.parametrize("kw,needle", [
     (dict(max_slots=0), "max_slots"),
     (dict(max_slots=5000), "max_slots"),
