@@ -184,10 +184,10 @@ int bn_selftest_wait_timeout(int32_t which, int64_t budget_cycles);
 int64_t bn_launch_counter(void);
 
 /* ---- kernel timing ------------------------------------------------------------------------ */
-/* When enabled, every sweep kernel launched for this sampler (or a batch containing it) is
- * bracketed by CUDA events on its stream; bn_kernel_times then returns, per kernel name, the
- * number of launches and their summed device time since the last read (and resets them).
- * Synchronises. */
+/* enable = 1: the evaluation kernel of every pass launched for this sampler (or a batch containing
+ * it) is bracketed by CUDA events on its stream; 2: every kernel of a pass; 0: none.
+ * bn_kernel_times then returns, per kernel name, the number of launches and their summed device
+ * time since the last read (and resets them).  Synchronises. */
 typedef struct bn_kernel_time {
     char name[32];
     int64_t launches;

@@ -1058,6 +1058,7 @@ int bn_set_kernel_timing(bn_sampler *s, int enable)
 {
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
     s->timer.enabled = enable != 0;
+    s->timer.detail = enable >= 2;
     return BN_OK;
 }
 

@@ -52,7 +52,8 @@ enum KernelKind { kKEvalPlain = 0, kKResolvePlain, kKCommitPlain, kKPersistent, 
 extern const char *const kKernelNames[kKindCount];
 
 struct KernelTimer {
-    bool enabled = false;
+    bool enabled = false;  // the evaluation kernel of every pass
+    bool detail = false;   // every kernel of a pass
     struct Rec {
         int kind;
         cudaEvent_t a, b;

@@ -254,12 +254,13 @@ cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTim
     else
         k_eval_plain<2><<<grid, kPlainThreads, 0, st>>>(sl.dprob);
     if (timed) tm->end(st);
-    if (timed) tm->begin(kKResolvePlain, st);
+    const bool all = timed && tm->detail;
+    if (all) tm->begin(kKResolvePlain, st);
     k_resolve_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
-    if (timed) tm->end(st);
-    if (timed) tm->begin(kKCommitPlain, st);
+    if (all) tm->end(st);
+    if (all) tm->begin(kKCommitPlain, st);
     k_commit_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);
-    if (timed) tm->end(st);
+    if (all) tm->end(st);
     note_launches(3);
     return cudaGetLastError();
 }
@@ -267,7 +268,7 @@ cudaError_t launch_plain_sweep(const SweepLaunch &sl, cudaStream_t st, KernelTim
 // the resolve and commit kernels alone (the tensor-core schedule evaluates couples itself)
 cudaError_t launch_resolve_commit(const SweepLaunch &sl, cudaStream_t st, KernelTimer *tm)
 {
-    const bool timed = tm && tm->enabled;
+    const bool timed = tm && tm->enabled && tm->detail;
     dim3 grid((sl.max_M + kPlainWarps - 1) / kPlainWarps, sl.n_prob);
     if (timed) tm->begin(kKResolvePlain, st);
     k_resolve_plain<<<grid, kPlainThreads, 0, st>>>(sl.dprob);

@@ -509,7 +509,7 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
             epi_sync();
             if (et < ncls) tab[pb.d2[et]] = et;
             epi_sync();
-            if (fast) {
+            if (fast && !colpath) {
                 const int dxm = tab2_dx(r), n2 = tw * (2 * tab2_dy(r) + 1);
                 for (int i = et; i < n2; i += kEpiThreads) {
                     const int dx = i % tw - dxm, dy = i / tw - tab2_dy(r);
@@ -724,7 +724,7 @@ __device__ __forceinline__ void note_patch(int (&idx)[kMaxMet], int (&dist)[kMax
 
 // One warp per couple: the couple's class sums are cleared, its f16 delta row k_b - k_a is
 // written for every stage, and each of its two pixels is appended to the lists of the patches
-// within the radius of it (lane 0: pixel a, lane 1: pixel b).
+// within the radius of it (lanes 0-15: pixel a, 16-31: pixel b, one patch per lane).
 __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
 {
     const Problem &pb = probs[blockIdx.y];
@@ -740,23 +740,27 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
     if (lane < 2 * kMaxClasses / 4)
         reinterpret_cast<int4 *>(pb.side_cls + (size_t)j * 2 * kMaxClasses)[lane] =
             make_int4(0, 0, 0, 0);
-    // deltas: piece v = 8 integrands of stage v / 8
-    const int nv = (pb.row_bytes >> 6) * 8;
+    // deltas, 16 integrands (two f16 pieces of one stage) per lane and step
+    const int nv = (pb.row_bytes >> 6) * 4;
     for (int v = lane; v < nv; v += 32) {
-        const int e0 = v * 8;  // first integrand of the piece
+        const int e0 = v * 16;  // first integrand
         const size_t cb = ((size_t)(e0 >> 7) * pb.P) << 7;
-        const uint2 ka = *reinterpret_cast<const uint2 *>(pb.counts + cb + ((size_t)a << 7) +
+        const uint4 ka = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)a << 7) +
                                                           (e0 & 127));
-        const uint2 kb = *reinterpret_cast<const uint2 *>(pb.counts + cb + ((size_t)b << 7) +
+        const uint4 kb = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)b << 7) +
                                                           (e0 & 127));
-        uint4 o;
-        bytes_sub_h2(kb.x, ka.x, o.x, o.y);
-        bytes_sub_h2(kb.y, ka.y, o.z, o.w);
-        *reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(v >> 3) * pb.M + j) << 6) +
-                                   (v & 7) * 8) = o;
+        uint4 o0, o1;
+        bytes_sub_h2(kb.x, ka.x, o0.x, o0.y);
+        bytes_sub_h2(kb.y, ka.y, o0.z, o0.w);
+        bytes_sub_h2(kb.z, ka.z, o1.x, o1.y);
+        bytes_sub_h2(kb.w, ka.w, o1.z, o1.w);
+        uint4 *dst = reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(v >> 2) * pb.M + j) << 6) +
+                                               (v & 3) * 16);
+        dst[0] = o0;
+        dst[1] = o1;
     }
-    if (lane >= 2) return;
-    const int side = lane;
+    // lanes 0..15 list pixel a, lanes 16..31 pixel b, one patch each, all atomics in parallel
+    const int side = lane >> 4, k = lane & 15;
     const int r = pb.radius, r2 = r * r;
     const int p = side ? b : a, px = p % pb.W, py = p / pb.W;
     // distinct patch columns (rows) met by x in [px - r, px + r] (y likewise), torus-wrapped,
@@ -768,9 +772,10 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
         note_patch(xi, xd, nx, wrap_add(px, dd, pb.W) / kPW, ad);
         note_patch(yi, yd, ny, wrap_add(py, dd, pb.H) / kPH, ad);
     }
-    for (int u = 0; u < nx; ++u)
-        for (int w = 0; w < ny; ++w) {
-            if (xd[u] * xd[u] + yd[w] * yd[w] > r2) continue;  // patch out of reach
+    // at most 3 x 4 patches for radius <= 8; the loop covers any count
+    for (int kk = k; kk < nx * ny; kk += 16) {
+        const int u = kk / ny, w = kk - (kk / ny) * ny;  // this lane's patch
+        if (xd[u] * xd[u] + yd[w] * yd[w] <= r2) {  // in reach
             const int pid = yi[w] * pb.tc_npx + xi[u];
             const int pos = atomicAdd(pb.tc_cnt + pid, 1);
             // min-image offset of p from the patch centre
@@ -783,6 +788,7 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
                 pb.tc_list[(size_t)pid * pb.tc_cap + pos] =
                     make_int4(p, side ? a : b, 2 * j + side, (rx & 0xFFFF) | (ry << 16));
         }
+    }
 }
 
 // f16 copy of the counts: piece v of the copy = 8 integrands of one pixel and stage
@@ -884,10 +890,10 @@ cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm
 {
     const dim3 gl((tl.max_M + kListThreads - 1) / kListThreads, tl.n_prob);
     const dim3 gw((tl.max_M + kListThreads / 32 - 1) / (kListThreads / 32), tl.n_prob);
-    const bool timed = tm && tm->enabled;
-    if (timed) tm->begin(kKTcLists, st);
+    const bool timed = tm && tm->enabled, all = timed && tm->detail;
+    if (all) tm->begin(kKTcLists, st);
     k_tc_lists<<<gw, kListThreads, 0, st>>>(tl.dprob);
-    if (timed) tm->end(st);
+    if (all) tm->end(st);
     if (tl.total_units > 0) {
         const TcArgs a{tl.dprob, tl.n_prob, tl.unit_start, tl.total_units};
         const int grid = tl.total_units < tl.sms ? tl.total_units : tl.sms;
@@ -896,9 +902,9 @@ cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm
         if (timed) tm->end(st);
         note_launches(1);
     }
-    if (timed) tm->begin(kKTcFinalize, st);
+    if (all) tm->begin(kKTcFinalize, st);
     k_tc_finalize<<<gl, kListThreads, 0, st>>>(tl.dprob);
-    if (timed) tm->end(st);
+    if (all) tm->end(st);
     note_launches(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -123,7 +123,8 @@ class Sampler:
     def reset(self, seed: int) -> None:
         L.check(L.load().bn_sampler_reset(self._h, seed))
 
-    def set_kernel_timing(self, enable: bool) -> None:
+    def set_kernel_timing(self, enable) -> None:
+        """True or 1: time the evaluation kernel of every pass; 2: every kernel; 0: none."""
         L.check(L.load().bn_set_kernel_timing(self._h, int(enable)))
 
     def kernel_times(self) -> dict:
