@@ -14,20 +14,24 @@
 // (T N^2 <= 2^24 for 8-bit counts), so every kept entry is an exact integer.
 //
 // A pass:
-//   k_tc_lists     couples of the pass as in the plain schedule; each proposed pixel is appended
-//                  to the list of every patch within the radius of it; its class sums cleared
+//   k_tc_lists     one warp per couple of the pass (as in the plain schedule): its class sums
+//                  cleared, its f16 delta row k_b - k_a written for every stage, and each of its
+//                  pixels appended to the list of every patch within the radius of it
 //   k_tc_stencil   one CTA per SM over the patches, warp-specialised:
-//                    9 producer warps   count bytes -> shared memory (cp.async, eight whole
-//                                       rows per warp instruction), converted in place to f16
-//                                       in the 128-byte swizzled K-major layout, deltas formed
-//                                       on the way; stages of 64 integrands
+//                    9 producer warps   cp.async of whole 128-byte rows (four per warp
+//                                       instruction) of the f16 count copy (A) and of the
+//                                       delta rows (B) straight into the 128-byte swizzled
+//                                       K-major layout; stages of 64 integrands
 //                    1 MMA warp         four tcgen05.mma (K = 16 each) per stage
-//                    4 epilogue warps   tensor memory -> registers; entries inside the radius
-//                                       go to per-pixel class sums in shared memory, then to
-//                                       the global class sums (integer atomics)
+//                    4 epilogue warps   tensor memory -> registers; for radius 6 a transpose
+//                                       of 32 columns through shared memory, each warp summing
+//                                       a quarter of the stencil offsets per listed pixel with
+//                                       compile-time classes; other radii a 2-D class table per
+//                                       entry; class sums to global memory (integer reductions)
 //                  five stages in a ring, two accumulator buffers in tensor memory
 //   k_tc_finalize  change of Eq. 1 from the class sums, flags and pixel claims
-//   then the resolve and commit kernels of the plain schedule.
+//   then the resolve and commit kernels of the plain schedule (the commit also swaps the f16
+//   copy, which k_tc_refresh rebuilds from the counts at the start of every run).
 // Every wait is bounded; a wait that runs out raises the problems' error word and the CTA
 // drains its copies and products, frees its tensor memory and returns.
 #include <utility>
@@ -45,7 +49,7 @@ constexpr int kLook = 3;                             // stages in flight per pro
 constexpr int kAStage = kTcM * 128;                  // 16 KB: 128 rows x 64 f16
 constexpr int kBStage = kNB * 128;                   // 20 KB: 160 rows x 64 f16
 constexpr int kStageBytes = kAStage + kBStage;
-constexpr int kEpiWarps = 4, kProdWarps = (kTcM + kNB) / 32;  // four pieces per thread
+constexpr int kEpiWarps = 4, kProdWarps = (kTcM + kNB) / 32;  // eight pieces per thread
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
