@@ -150,3 +150,19 @@ def test_workload_definitions():
     # every workload is a valid configuration: 24 T N^2 < 2^31
     for t in c4 + [c3] + wl.c2() + wl.c1():
         assert 24 * t.n_integrands * t.n_points ** 2 < 2 ** 31
+
+
+def test_measured_peak_reads_the_driver_file_or_falls_back(tmp_path, monkeypatch):
+    val, how = bench.measured_peak("bf16_tflops")
+    path = os.path.join(os.path.dirname(os.path.abspath(bench.__file__)), "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        import json
+        assert how == "of measured" and val == float(json.load(open(path))["bf16_tflops"])
+    else:
+        assert how == "of fallback" and val == 1900.0
+    # an unreadable or incomplete file falls back to the recipe's figures
+    monkeypatch.setattr(bench.os.path, "dirname", lambda _p: str(tmp_path))
+    assert bench.measured_peak("hbm_gbs") == (6800.0, "of fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 7000}')
+    assert bench.measured_peak("hbm_gbs") == (7000.0, "of measured")
+    assert bench.measured_peak("bf16_tflops") == (1900.0, "of fallback")
