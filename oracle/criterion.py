@@ -1,6 +1,6 @@
 """CPU oracle of the sampler-evaluation criterion (test infrastructure only).
 
-Sec. 3.3: a screen-space sampler is judged by how much error is left after denoising; the
+Sec. 3.3: a screen-space sampler is rated by how much error is left after denoising; the
 denoiser is stood in for by Gaussian filters of standard deviation sigma in [0.25, 20] applied to
 the tile of Monte-Carlo estimates of the test integrands, and the criterion is the RMSE of the
 filtered estimates against the exact integrals, ||(I_N * k_sigma) - I_ref|| (Fig. 1c).
