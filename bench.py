@@ -310,6 +310,19 @@ def workload_tiles(args):
 SCHEDULE_NAMES = {1: "plain", 2: "persistent", 3: "tensor"}
 
 
+def schedule_desc(chosen: dict) -> dict:
+    """The chosen schedule for the JSON line (CTA shape and chunk split: persistent only)."""
+    kind = SCHEDULE_NAMES.get(chosen["kind"], "?")
+    out = {"kind": kind}
+    if kind == "persistent":
+        out.update({"block": list(chosen["shape"][:2]), "threads": chosen["shape"][2],
+                    "tsplit": chosen["tsplit"]})
+    if kind == "tensor":
+        out["product"] = "tcgen05.mma kind::f16, M = 128 patch pixels, N <= 160, K = 16"
+    out["chosen_by"] = chosen.get("chosen_by", "autotuner")
+    return out
+
+
 def measured_peak(key: str):
     """(value, provenance) of a peak from the measured file, else the recipe fallback."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
@@ -507,10 +520,7 @@ def run_ours(args) -> int:
             "data": "synthetic",
             "config": {"workload": desc, "tiles_per_gpu": B, "sweeps": sweeps,
                        "schedule": args.schedule if chosen is None else
-                       {"kind": SCHEDULE_NAMES.get(chosen["kind"], "?"),
-                        "block": chosen["shape"][:2],
-                        "threads": chosen["shape"][2], "tsplit": chosen["tsplit"],
-                        "chosen_by": chosen.get("chosen_by", "autotuner")},
+                       schedule_desc(chosen),
                        "parallelism": f"independent tiles x{world}",
                        "l2": "flushed between steps (256 MB write)"},
             "tiles_per_s": world * B * args.steps / (total_ms / 1000.0),

@@ -166,3 +166,13 @@ def test_measured_peak_reads_the_driver_file_or_falls_back(tmp_path, monkeypatch
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 7000}')
     assert bench.measured_peak("hbm_gbs") == (7000.0, "of measured")
     assert bench.measured_peak("bf16_tflops") == (1900.0, "of fallback")
+
+
+def test_schedule_description_of_the_json_line():
+    t = bench.schedule_desc({"kind": 3, "shape": (0, 0, 0, 0), "tsplit": 0})
+    assert t["kind"] == "tensor" and "block" not in t and t["chosen_by"] == "autotuner"
+    p = bench.schedule_desc({"kind": 2, "shape": (8, 8, 256, 4), "tsplit": 1,
+                             "chosen_by": "command line"})
+    assert p == {"kind": "persistent", "block": [8, 8], "threads": 256, "tsplit": 1,
+                 "chosen_by": "command line"}
+    assert bench.schedule_desc({"kind": 1, "shape": (0, 0, 0, 0), "tsplit": 0})["kind"] == "plain"
