@@ -49,6 +49,9 @@ REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 # of k_persistent for 128x128 N=64 T=1024); a launch's traffic scales with its tile-passes
 TRAFFIC_PER_TILE_PASS = (1683.924e6 + 58.356e6) / (16 * 6)
 PASSES_PER_LAUNCH = 500
+# k_tc_stencil, 128x128 N=64 T=1024: ncu dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch over 16 tiles (616.0 MB + 8.0 MB), per tile
+TC_TRAFFIC_PER_TILE_PASS = (616.029e6 + 7.991e6) / 16
 # shared-memory wavefront rate: 128 B per SM clock, measured 120 B/clk/SM by a probe
 SMEM_PEAK_TBS = 152 * 120 * 2.07e9 / 1e12
 
@@ -481,6 +484,11 @@ def run_ours(args) -> int:
                     "launches": nl, "avg_launch_ms": tms / nl,
                     "share": tms / max(sum(v[1] for v in ktimes.values()), 1e-9)}
         if name == "stencil_tensor":
+            if args.workload == "c2" and not wide:
+                traffic = TC_TRAFFIC_PER_TILE_PASS * B
+                roofline["traffic"] = traffic
+                roofline["traffic_note"] = ("DRAM bytes per launch (one pass), scaled by tiles "
+                                            "from an ncu capture of 16 tiles")
             # the tensor-core stencil: f16 products on the tensor pipe; useful FLOPs (2 per
             # multiply-accumulate kept by the stencil) against the measured dense bf16 peak
             # (f16 runs at the bf16 rate); the products outside the radius are not counted
