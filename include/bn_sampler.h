@@ -203,7 +203,11 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
  * tiles gives way to the first one that does); tsplit = chunk ranges per block
  * (1..4, 0 = auto).  8x8/512/4 evaluates 8-bit counts on the tensor cores (mma.sync f16, exact
  * for N <= 64) and needs tile sides that are multiples of 8, at least 24.  block_x = 0 keeps the
- * default shape.  set synchronises the stream. */
+ * default shape.  BN_SCHEDULE_TENSOR ignores the other fields; it needs 8-bit counts (N <= 64),
+ * radius <= 8 and tile sides of at least 2 radius + 1 for every problem (BN_ERR_INVALID_ARG
+ * otherwise), and its plan holds an f16 copy of the counts and the couples' per-pass f16
+ * deltas (2 x and 1/4 x the count bytes for T = 1024 on a 128 x 128 tile), released with the
+ * plan.  set synchronises the stream. */
 typedef struct bn_schedule {
     int32_t kind;
     int32_t block_x, block_y;
