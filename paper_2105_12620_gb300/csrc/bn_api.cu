@@ -1245,8 +1245,14 @@ int autotune(const std::vector<bn_sampler *> &members, int32_t trial_sweeps, cud
         if (!fits) continue;
         if (c.kind == BN_SCHEDULE_PLAIN && best_ms >= 0.f) continue;  // plain only as fallback
         if ((rc = make_plan(hp, dp, c.kind, c.kind == BN_SCHEDULE_PERSISTENT ? &shape : nullptr,
-                            plan)))
-            break;
+                            plan))) {
+            if (c.kind != BN_SCHEDULE_TENSOR) break;
+            // the tensor-core plan could not allocate its f16 copies: not a candidate here
+            cudaGetLastError();
+            free_plan(plan);
+            rc = BN_OK;
+            continue;
+        }
         if ((rc = run_plan(plan, dp, hp, 2, st, nullptr))) break;  // warm
         cudaEventRecord(e0, st);
         if ((rc = run_plan(plan, dp, hp, trial_sweeps, st, nullptr))) break;
