@@ -1102,7 +1102,14 @@ static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Pro
     if (want_shape && !known)
         return fail(BN_ERR_INVALID_ARG, "no kernel instantiated for block %dx%d, %d threads, %d "
                     "slots per warp", sc->block_x, sc->block_y, sc->threads, sc->slots_per_warp);
-    return make_plan(hp, dprob, sc->kind, want_shape ? &shape : nullptr, plan);
+    const int rc = make_plan(hp, dprob, sc->kind, want_shape ? &shape : nullptr, plan);
+    if (rc) {  // the previous plan is gone: leave the default one so the object stays usable
+        const std::string msg = g_error;
+        cudaGetLastError();
+        make_plan(hp, dprob, BN_SCHEDULE_AUTO, nullptr, plan);
+        return fail(rc, "%s", msg.c_str());
+    }
+    return BN_OK;
 }
 
 static void get_schedule_common(const SweepPlan &pl, bn_schedule *out)
@@ -1341,9 +1348,9 @@ int bn_sampler_set_schedule(bn_sampler *s, const bn_schedule *sc)
     if (!s) return fail(BN_ERR_INVALID_ARG, "null sampler");
     if (int rc = set_device(s)) return rc;
     BN_CUDA(cudaStreamSynchronize(s->stream));
-    if (int rc = set_schedule_common(s->hprob, s->dprob, sc, s->plan)) return rc;
+    const int rc = set_schedule_common(s->hprob, s->dprob, sc, s->plan);
     s->schedule = plan_kind(s->plan);
-    return BN_OK;
+    return rc;
 }
 
 int bn_sampler_get_schedule(bn_sampler *s, bn_schedule *out)

@@ -187,6 +187,11 @@ def test_tensor_schedule_refused_outside_its_domain(pkg, W, H, N, T, r):
     s = pkg.Sampler(W, H, N, T, seed=1, radius=r)
     with pytest.raises(BnError):
         s.set_schedule(pkg.BN_SCHEDULE_TENSOR)
+    # the sampler keeps a usable default schedule and still runs its passes
+    assert s.get_schedule()["kind"] in (pkg.BN_SCHEDULE_PERSISTENT, pkg.BN_SCHEDULE_PLAIN)
+    sw = s.get_state()[0]
+    st = s.optimize(3)
+    assert st.sweeps == 3 and s.get_state()[0] == sw + 3
     s.close()
 
 
