@@ -27,7 +27,7 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t k
 }
 
 // shared-memory descriptor of slice k16 (0..3) of a swizzled K-major tile at shared address base
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t base, int k16)
+__host__ __device__ __forceinline__ uint64_t sw128_desc(uint32_t base, int k16)
 {
     const uint32_t start = base + (uint32_t)k16 * 32u;
     uint64_t d = (uint64_t)((start >> 4) & 0x3FFFu);
