@@ -49,9 +49,6 @@ REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 # of k_persistent for 128x128 N=64 T=1024); a launch's traffic scales with its tile-passes
 TRAFFIC_PER_TILE_PASS = (1683.924e6 + 58.356e6) / (16 * 6)
 PASSES_PER_LAUNCH = 500
-# k_tc_stencil, 128x128 N=64 T=1024: ncu dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch over 16 tiles (616.0 MB + 8.0 MB), per tile
-TC_TRAFFIC_PER_TILE_PASS = (616.029e6 + 7.991e6) / 16
 # shared-memory wavefront rate: 128 B per SM clock, measured 120 B/clk/SM by a probe
 SMEM_PEAK_TBS = 152 * 120 * 2.07e9 / 1e12
 
@@ -333,7 +330,67 @@ def measured_peak(key: str):
         with open(path) as f:
             return float(json.load(f)[key]), "of measured"
     except (OSError, KeyError, ValueError):
-        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}[key], "of fallback"
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "hbm_gbs": 6800.0}[key], "of fallback"
+
+
+def kernel_roofline(ktimes: dict, specs, split_steps: int, sweeps: int, args, chosen, pkg):
+    """Roofline of the dominant kernel of the kernel-split run.
+
+    Algorithmic work of a proposal: 2 sides x 112 neighbours x T multiply-accumulates (the
+    swap terms of Eq. 1).  Algorithmic bytes of a tile-pass: the P x T count bytes every pass
+    must read (every pixel neighbours some proposed pixel).  Both over the kernel's average
+    launch duration (CUDA events on its stream)."""
+    if not ktimes:
+        return None
+    name, (nl, tms) = max(ktimes.items(), key=lambda kv: kv[1][1])
+    total_ops = split_steps * sum(t.proposals() * 2 * STENCIL_OFFSETS * t.n_integrands
+                                  for t in specs)
+    count_bytes = split_steps * sweeps * sum(
+        t.width * t.height * t.n_integrands * (2 if t.n_points > 64 else 1) * t.n_pairs
+        for t in specs)
+    wide = any(t.n_points > 64 for t in specs)
+    secs = tms / 1000.0
+    hbm_peak, hbm_src = measured_peak("hbm_gbs")
+    all_ms = sum(v[1] for v in ktimes.values())
+    hbm = {"achieved": count_bytes / secs / 1e9, "peak": hbm_peak, "unit": "GB/s",
+           "frac": count_bytes / secs / 1e9 / hbm_peak,
+           "pass_frac": count_bytes / (all_ms / 1000.0) / 1e9 / hbm_peak,
+           "note": "algorithmic bytes: the P x T count bytes a pass reads, over this kernel's "
+                   "time (frac) and over every kernel of the pass (pass_frac); peak = HBM copy "
+                   + hbm_src}
+    if name == "stencil_tensor":
+        # f16 products on the tensor pipe: useful FLOPs (2 per multiply-accumulate the stencil
+        # keeps; the products outside the radius are not counted) against the measured dense
+        # bf16 peak sustained over seconds (the kernel runs inside a seconds-long step; f16
+        # runs at the bf16 rate)
+        tpeak, tsrc = measured_peak("bf16_tflops_sustained")
+        tf = 2.0 * total_ops / secs / 1e12
+        alu_peak = IMAD_PEAK_TOPS if wide else DP4A_PEAK_TOPS
+        return {"kernel": name, "bound": "tensor", "achieved": tf, "peak": tpeak,
+                "unit": "TFLOP/s", "frac": tf / tpeak, "traffic": None,
+                "note": "useful f16 FLOPs of the stencil (2 per kept product); peak = dense "
+                        "bf16 sustained " + tsrc,
+                "launches": nl, "avg_launch_ms": tms / nl, "share": tms / max(all_ms, 1e-9),
+                "hbm": hbm,
+                "int8_equivalent": {"achieved": total_ops / secs / 1e12, "peak": alu_peak,
+                                    "unit": "TOP/s",
+                                    "frac": total_ops / secs / 1e12 / alu_peak}}
+    peak = IMAD_PEAK_TOPS if wide else DP4A_PEAK_TOPS
+    achieved = total_ops / secs / 1e12
+    traffic = None
+    sched = chosen or {}
+    if (args.workload == "c2" and not wide and sched.get("kind") == pkg.BN_SCHEDULE_PERSISTENT
+            and tuple(sched.get("shape", ())[:2]) == (8, 8)):
+        traffic = TRAFFIC_PER_TILE_PASS * len(specs) * min(sweeps, PASSES_PER_LAUNCH)
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TOP/s", "frac": achieved / peak, "traffic": traffic,
+            "note": ("op = one int16 multiply-accumulate; peak = IMAD nominal "
+                     "(152 SMs x 64/clk x 2.07 GHz)") if wide else
+                    ("op = one int8 multiply-accumulate; peak = IDP4A nominal "
+                     "(152 SMs x 64/clk x 4 x 2.07 GHz)"),
+            "launches": nl, "avg_launch_ms": tms / nl, "share": tms / max(all_ms, 1e-9),
+            "hbm": hbm}
 
 
 def run_ours(args) -> int:
@@ -412,8 +469,8 @@ def run_ours(args) -> int:
             flush.zero_()
             step(k)
         stream.synchronize()
-        tiles[0].set_kernel_timing(True)
-        tiles[0].kernel_times()
+        # timed region: the library as a user runs it (sweeps replayed from CUDA graphs, no
+        # per-kernel events)
         launches0 = L.load().bn_launch_counter()
         clocks = ClockSampler()
         if dist is not None:
@@ -430,10 +487,25 @@ def run_ours(args) -> int:
         torch.cuda.synchronize()
         clock_info = clocks.stop(physical_gpu_index(local))
         launches = L.load().bn_launch_counter() - launches0
-        ktimes = tiles[0].kernel_times()
-        tiles[0].set_kernel_timing(False)
         step_ms = [a.elapsed_time(b) for a, b in ev]
         local_ms = sum(step_ms)
+        # kernel split: the same steps once more with every kernel of a pass bracketed by CUDA
+        # events on the launching stream (direct launches: events cannot sit between the
+        # kernels of a replayed graph); the dominant kernel's duration for the roofline
+        split_steps = min(args.steps, args.split_steps)
+        tiles[0].set_kernel_timing(2)
+        tiles[0].kernel_times()
+        split_ms = 0.0
+        for k in range(split_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(args.warmup + args.steps + k)
+            b.record(stream)
+            b.synchronize()
+            split_ms += a.elapsed_time(b)
+        ktimes = tiles[0].kernel_times()
+        tiles[0].set_kernel_timing(False)
         # end to end through the public API with host buffers (pinned staging inside)
         e2e_ms = []
         for k in range(args.steps):
@@ -451,56 +523,8 @@ def run_ours(args) -> int:
     props_step = sum(t.proposals() for t in specs)
     value = world * props_step * args.steps / (total_ms / 1000.0)
     e2e_value = world * props_step * args.steps / (e2e_total / 1000.0)
+    roofline = kernel_roofline(ktimes, specs, split_steps, sweeps, args, chosen, pkg)
 
-    # dominant kernel and its roofline: algorithmic multiply-accumulates of the couples' swap
-    # terms, 2 sides x 112 neighbours x T per proposal, over that kernel's measured time
-    dom = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
-    roofline = None
-    if dom:
-        name, (nl, tms) = dom
-        total_ops = args.steps * sum(t.proposals() * 2 * STENCIL_OFFSETS * t.n_integrands
-                                     for t in specs)
-        wide = any(t.n_points > 64 for t in specs)
-        peak = IMAD_PEAK_TOPS if wide else DP4A_PEAK_TOPS
-        achieved = total_ops / (tms / 1000.0) / 1e12
-        traffic = None
-        sched = chosen or {}
-        if (args.workload == "c2" and not wide and sched.get("kind") == pkg.BN_SCHEDULE_PERSISTENT
-                and tuple(sched.get("shape", ())[:2]) == (8, 8)):
-            traffic = TRAFFIC_PER_TILE_PASS * B * min(sweeps, PASSES_PER_LAUNCH)
-        roofline = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "TOP/s", "frac": achieved / peak, "traffic": traffic,
-                    "traffic_note": "DRAM bytes per launch, scaled by tile-passes from an ncu "
-                                    "capture of 16 tiles x 6 passes" if traffic else None,
-                    "smem": {"achieved": achieved, "peak": SMEM_PEAK_TBS, "unit": "TB/s",
-                             "frac": achieved / SMEM_PEAK_TBS,
-                             "note": "the stencil reads one shared-memory byte per "
-                                     "multiply-accumulate; peak = probed wavefront rate"}
-                    if not wide else None,
-                    "note": ("op = one int16 multiply-accumulate; peak = IMAD nominal "
-                             "(152 SMs x 64/clk x 2.07 GHz)") if wide else
-                            ("op = one int8 multiply-accumulate; peak = IDP4A nominal "
-                             "(152 SMs x 64/clk x 4 x 2.07 GHz)"),
-                    "launches": nl, "avg_launch_ms": tms / nl,
-                    "share": tms / max(sum(v[1] for v in ktimes.values()), 1e-9)}
-        if name == "stencil_tensor":
-            if args.workload == "c2" and not wide:
-                traffic = TC_TRAFFIC_PER_TILE_PASS * B
-                roofline["traffic"] = traffic
-                roofline["traffic_note"] = ("DRAM bytes per launch (one pass), scaled by tiles "
-                                            "from an ncu capture of 16 tiles")
-            # the tensor-core stencil: f16 products on the tensor pipe; useful FLOPs (2 per
-            # multiply-accumulate kept by the stencil) against the measured dense bf16 peak
-            # (f16 runs at the bf16 rate); the products outside the radius are not counted
-            tpeak = measured_peak("bf16_tflops")
-            tf = 2.0 * total_ops / (tms / 1000.0) / 1e12
-            alu = dict(roofline)
-            roofline.update({"bound": "tensor", "achieved": tf, "unit": "TFLOP/s",
-                             "peak": tpeak[0], "frac": tf / tpeak[0], "smem": None,
-                             "note": "useful f16 FLOPs of the stencil (2 per kept product); "
-                                     "peak = dense bf16 " + tpeak[1],
-                             "int8_equivalent": {k: alu[k] for k in
-                                                 ("achieved", "peak", "unit", "frac")}})
     plain = None
     if not args.no_plain and rank == 0 and args.workload == "c2":
         plain = plain_per_tile(pkg, stream, rank)
@@ -529,6 +553,12 @@ def run_ours(args) -> int:
             "config": {"workload": desc, "tiles_per_gpu": B, "sweeps": sweeps,
                        "schedule": args.schedule if chosen is None else
                        schedule_desc(chosen),
+                       "objective": "raise Eq. 1 (blue-noise direction; the printed 'reduce' "
+                                    "is BN_OBJECTIVE_LITERAL)",
+                       "commit": "non-interacting improving couples",
+                       "timing": "device events around each step; sweeps replayed from CUDA "
+                                 "graphs; kernel split from %d further steps with every kernel "
+                                 "bracketed by events" % split_steps,
                        "parallelism": f"independent tiles x{world}",
                        "l2": "flushed between steps (256 MB write)"},
             "tiles_per_s": world * B * args.steps / (total_ms / 1000.0),
@@ -539,6 +569,7 @@ def run_ours(args) -> int:
             "clocks": {k: clock_info[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "roofline": roofline,
             "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in ktimes.items()},
+            "kernel_split_ms_per_step": split_ms / max(split_steps, 1),
             "cpu_baseline": cpu,
             "plain_per_tile": plain,
             "serving": serving,
@@ -678,6 +709,8 @@ def main(argv=None) -> int:
     ap.add_argument("--schedule", choices=["auto", "plain", "persistent", "tensor"],
                     default="auto")
     ap.add_argument("--cpu-sweeps", type=int, default=20)
+    ap.add_argument("--split-steps", type=int, default=2,
+                    help="steps of the kernel-split run (every kernel timed by events)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--block", default="", help="force a persistent CTA block, e.g. 8x8")

@@ -64,8 +64,8 @@ extern "C" {
 #define BN_SCHEDULE_PLAIN 1      /* three launches per sweep, one warp per couple           */
 #define BN_SCHEDULE_PERSISTENT 2 /* one cooperative launch for many sweeps, SMEM-blocked    */
 #define BN_SCHEDULE_TENSOR 3     /* five launches per sweep, the stencil of Eq. 1 as products */
-                                 /* on the 5th-generation tensor cores (8-bit counts, N <= 64,*/
-                                 /* tile sides >= 2 radius + 1)                               */
+                                 /* on the 5th-generation tensor cores (N <= 512 and         */
+                                 /* T N^2 <= 2^25, tile sides >= 2 radius + 1)               */
 
 typedef struct bn_config {
     int32_t width, height;     /* toroidal tile, 2..4096 each, width*height <= 2^22          */
@@ -203,11 +203,11 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
  * tiles gives way to the first one that does); tsplit = chunk ranges per block
  * (1..4, 0 = auto).  8x8/512/4 evaluates 8-bit counts on the tensor cores (mma.sync f16, exact
  * for N <= 64) and needs tile sides that are multiples of 8, at least 24.  block_x = 0 keeps the
- * default shape.  BN_SCHEDULE_TENSOR ignores the other fields; it needs 8-bit counts (N <= 64),
- * radius <= 8 and tile sides of at least 2 radius + 1 for every problem (BN_ERR_INVALID_ARG
- * otherwise), and its plan holds an f16 copy of the counts and the couples' per-pass f16
- * deltas (2 x and 1/4 x the count bytes for T = 1024 on a 128 x 128 tile), released with the
- * plan.  set synchronises the stream. */
+ * default shape.  BN_SCHEDULE_TENSOR ignores the other fields; for every problem it needs counts
+ * below 1024 (N <= 512), centred products that stay exact in f32 (T N^2 <= 2^25), radius <= 8
+ * and tile sides of at least 2 radius + 1 (BN_ERR_INVALID_ARG otherwise); its plan holds the
+ * couples' per-pass f16 deltas (1/4 of the count bytes for 8-bit counts, 1/8 for 16-bit) and one
+ * TMA tensor map per problem, released with the plan.  set synchronises the stream. */
 typedef struct bn_schedule {
     int32_t kind;
     int32_t block_x, block_y;
@@ -361,8 +361,13 @@ void bn_server_destroy(bn_server *sv);
  *   width, height, n_points, n_integrands, sigma, radius: as in bn_config (radius 1..8)
  * Enqueued on cuda_stream; returns without waiting.  The first call on each device looks up
  * the device address of the scratch array (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  Every call shares the scratch array: a call clears what it uses
- * before accumulating, but calls whose work overlaps on the GPU race on it. */
+ * before any stream capture.  That address is kept for the life of the process: after a reset
+ * of the device's context (cudaDeviceReset, or a primary-context reset by the host framework)
+ * the module is reloaded and the cached address is stale, so do not call this entry point
+ * again after such a reset.  Every call shares the scratch array: a call clears what it uses
+ * before accumulating, but calls whose work overlaps on the GPU race on it.  A CUDA error
+ * already pending on the calling thread is reported (BN_ERR_CUDA) before anything is launched,
+ * and is left pending for the caller. */
 int bn_evaluate_energy_noalloc(const int32_t *counts, int32_t n_fields, int32_t width,
                                int32_t height, int32_t n_points, int32_t n_integrands,
                                float sigma, int32_t radius, double *energy, void *cuda_stream);

@@ -103,12 +103,13 @@ namespace {
 
 // How the passes of a set of problems are executed, and the device arrays that go with it.
 struct SweepPlan {
+    bool ready = false;             // built completely; a failed build leaves an empty plan
     bool persistent = false;
-    bool tensor = false;            // tensor-core schedule (every problem has 8-bit counts)
+    bool tensor = false;            // tensor-core schedule (every problem supports it)
     int *d_tc_prefix = nullptr;     // [n_prob + 1] prefix sums of 16 x 8 patches
     int tc_units = 0;
-    // the problems as the tensor-core kernels see them: the same state plus the plan's f16
-    // count copies and per-pass delta rows (allocations in tc_bufs)
+    // the problems as the tensor-core kernels see them: the same state plus the plan's per-pass
+    // f16 delta rows (allocations in tc_bufs)
     bn::Problem *d_tcprob = nullptr;
     std::vector<bn::Problem> tcprob;
     std::vector<void *> tc_bufs;
@@ -119,7 +120,7 @@ struct SweepPlan {
     int *d_prefix = nullptr;        // [2][2][n_prob + 1] unit / couple prefix sums
     bn::GridBarrier *d_bar = nullptr;
     int *d_work = nullptr;          // [2] phase-1 unit counters
-    char *d_tmaps = nullptr;        // [n_prob] TMA tensor maps (tensor-core shape only)
+    char *d_tmaps = nullptr;        // TMA tensor maps of the count planes (tensor-core plans)
     int n_prob = 0, max_M = 0, sms = 0;
     // plain schedule: passes per captured CUDA graph (0 = launch every kernel directly); the
     // graphs hold the problem pointers, so they live and die with the plan
@@ -148,6 +149,7 @@ void free_plan(SweepPlan &pl)
     for (void *b : pl.tc_bufs) cudaFree(b);
     pl.tc_bufs.clear();
     pl.tcprob.clear();
+    pl.ready = false;
     pl.tensor = false;
     pl.persistent = false;
     pl.tc_units = 0;
@@ -391,8 +393,8 @@ int check_device_error(const bn_sampler *s)
 // Build the execution plan of a problem list (grouped by count width, 1-byte group first).
 // schedule: BN_SCHEDULE_*; the persistent schedule needs the radius-6 stencil on tiles of at
 // least 13 x 13 for every problem.
-int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int schedule,
-              const bn::PersistentShape *want, SweepPlan &pl)
+int build_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int schedule,
+               const bn::PersistentShape *want, SweepPlan &pl)
 {
     free_plan(pl);
     pl.n_prob = (int)hp.size();
@@ -404,22 +406,28 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
     if (schedule == BN_SCHEDULE_TENSOR) {
         for (auto &h : hp)
             if (!bn::tc_supported(h))
-                return fail(BN_ERR_INVALID_ARG, "the tensor-core schedule needs 8-bit counts "
-                            "(N <= 64) and tile sides of at least 2 radius + 1");
+                return fail(BN_ERR_INVALID_ARG, "the tensor-core schedule needs counts below "
+                            "1024 (N <= 512), exact centred products (T N^2 <= 2^25), radius "
+                            "<= 8 and tile sides of at least 2 radius + 1");
         std::vector<int> pre((size_t)pl.n_prob + 1, 0);
         for (int i = 0; i < pl.n_prob; ++i) pre[i + 1] = pre[i] + bn::tc_units_per_problem(hp[i]);
         pl.tc_units = pre[pl.n_prob];
         BN_CUDA(bn::prepare_tc());
         pl.tcprob = hp;
-        for (auto &h : pl.tcprob) {
-            void *m = nullptr, *d = nullptr;
-            BN_CUDA(cudaMalloc(&m, (size_t)h.P * h.row_bytes * 2));
-            pl.tc_bufs.push_back(m);
-            BN_CUDA(cudaMalloc(&d, (size_t)h.M * h.row_bytes * 2));
+        const size_t mb = (size_t)bn::tc_tensor_map_bytes();
+        std::vector<char> maps((size_t)pl.n_prob * mb, 0);
+        for (size_t i = 0; i < pl.tcprob.size(); ++i) {
+            bn::Problem &h = pl.tcprob[i];
+            void *d = nullptr;
+            BN_CUDA(cudaMalloc(&d, bn::tc_delta_bytes(h)));
             pl.tc_bufs.push_back(d);
-            h.tc_counts16 = static_cast<uint16_t *>(m);
             h.tc_delta16 = static_cast<uint16_t *>(d);
+            if (bn::encode_tc_tensor_map(h, maps.data() + i * mb) != cudaSuccess)
+                return fail(BN_ERR_INVALID_ARG, "tensor map of the count planes could not be "
+                            "encoded (%d x %d tile)", h.W, h.H);
         }
+        BN_CUDA(cudaMalloc(&pl.d_tmaps, maps.size()));
+        BN_CUDA(cudaMemcpy(pl.d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
         BN_CUDA(cudaMalloc(&pl.d_tcprob, sizeof(bn::Problem) * pl.tcprob.size()));
         BN_CUDA(cudaMemcpy(pl.d_tcprob, pl.tcprob.data(), sizeof(bn::Problem) * pl.tcprob.size(),
                            cudaMemcpyHostToDevice));
@@ -522,6 +530,23 @@ int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int 
     return BN_OK;
 }
 
+// A build that fails at any step (an allocation, a tensor-map encoding, an unsupported tile)
+// leaves an empty plan that every sweep call refuses, never a half-built one whose kernels would
+// be handed null device arrays.
+int make_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int schedule,
+              const bn::PersistentShape *want, SweepPlan &pl)
+{
+    const int rc = build_plan(hp, dprob, schedule, want, pl);
+    if (rc) {
+        const std::string msg = g_error;
+        free_plan(pl);
+        cudaGetLastError();
+        return fail(rc, "%s", msg.c_str());
+    }
+    pl.ready = true;
+    return BN_OK;
+}
+
 constexpr int kItersPerLaunch = 500;
 
 int plan_kind(const SweepPlan &pl)
@@ -535,7 +560,8 @@ cudaError_t launch_pass(const SweepPlan &pl, const bn::SweepLaunch &sl, cudaStre
                         bn::KernelTimer *tm)
 {
     if (!pl.tensor) return bn::launch_plain_sweep(sl, st, tm);
-    const bn::TcLaunch tl{pl.d_tcprob, sl.n_prob, pl.max_M, pl.d_tc_prefix, pl.tc_units, pl.sms};
+    const bn::TcLaunch tl{pl.d_tcprob, sl.n_prob, pl.max_M, pl.d_tc_prefix, pl.tc_units, pl.sms,
+                          pl.d_tmaps};
     return bn::launch_tc_sweep(tl, st, tm);
 }
 
@@ -569,9 +595,10 @@ int capture_plain(SweepPlan &pl, const bn::SweepLaunch &sl, int g)
 int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Problem> &hp,
              int32_t n_sweeps, cudaStream_t st, bn::KernelTimer *tm, bool set_end = true)
 {
+    if (!pl.ready)
+        return fail(BN_ERR_BAD_STATE, "no usable execution plan (a schedule change failed and "
+                    "the default plan could not be rebuilt); reset or recreate the object");
     if (set_end) BN_CUDA(bn::launch_set_end(dprob, pl.n_prob, n_sweeps, 1, st));
-    if (pl.tensor && n_sweeps > 0)  // the f16 count copies follow whatever ran since
-        BN_CUDA(bn::launch_tc_refresh(pl.d_tcprob, pl.tcprob, st));
     if (!pl.persistent) {
         // per-kernel timing needs the individual launches
         const bool graphs = pl.graph_passes > 0 && !(tm && tm->enabled);
@@ -1106,7 +1133,9 @@ static int set_schedule_common(const std::vector<bn::Problem> &hp, const bn::Pro
     if (rc) {  // the previous plan is gone: leave the default one so the object stays usable
         const std::string msg = g_error;
         cudaGetLastError();
-        make_plan(hp, dprob, BN_SCHEDULE_AUTO, nullptr, plan);
+        if (make_plan(hp, dprob, BN_SCHEDULE_AUTO, nullptr, plan) != BN_OK)
+            return fail(rc, "%s (and the default plan could not be rebuilt: %s; sweeps now "
+                        "return BN_ERR_BAD_STATE)", msg.c_str(), g_error.c_str());
         return fail(rc, "%s", msg.c_str());
     }
     return BN_OK;
@@ -1254,7 +1283,7 @@ int autotune(const std::vector<bn_sampler *> &members, int32_t trial_sweeps, cud
         if ((rc = make_plan(hp, dp, c.kind, c.kind == BN_SCHEDULE_PERSISTENT ? &shape : nullptr,
                             plan))) {
             if (c.kind != BN_SCHEDULE_TENSOR) break;
-            // the tensor-core plan could not allocate its f16 copies: not a candidate here
+            // the tensor-core plan could not allocate its delta rows: not a candidate here
             cudaGetLastError();
             free_plan(plan);
             rc = BN_OK;

@@ -64,10 +64,8 @@ struct Problem {
     int4 *tc_list;             // [tc_npx * tc_npy][tc_cap] (pixel, partner, slot 2 j + side,
                                // position relative to the patch centre), see bn_tc.cu
     int32_t tc_npx, tc_npy, tc_cap;  // patches of 16 x 8 pixels per row / column, list capacity
-    // tensor-core schedule only (owned by its plan, null elsewhere): f16 copy of the counts,
-    // [row_bytes / 64][P][64] (the commit keeps it in step), and per-pass f16 deltas
-    // k_b - k_a of the couples, [row_bytes / 64][M][64]
-    uint16_t *tc_counts16;
+    // tensor-core schedule only (owned by its plan, null elsewhere): per-pass f16 deltas
+    // k_b - k_a of the couples, [stages][M][64] with stages = row_bytes / (64 count_bytes)
     uint16_t *tc_delta16;
     long long *ctr;            // [0] pass counter, [1] pass end, [2] ticket
     unsigned long long *stats; // [kStatCount]

@@ -85,21 +85,25 @@ cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int r
 cudaError_t launch_set_ends(const Problem *dprob, int n_prob, const int *n_sweeps_dev,
                             int reset_stats, cudaStream_t st);
 
-// tensor-core schedule (bn_tc.cu): 8-bit counts, radius <= 8, tile sides >= 2 radius + 1
+// tensor-core schedule (bn_tc.cu): 8-bit counts, or 16-bit counts with N <= 512; centred
+// products exact (T N^2 <= 2^25); radius <= 8; tile sides >= 2 radius + 1
 struct TcLaunch {
-    const Problem *dprob;   // device array of problems (all with 8-bit counts)
+    const Problem *dprob;   // device array of problems (each with its tc_delta16 buffer)
     int n_prob;
     int max_M;
     const int *unit_start;  // device [n_prob + 1] prefix sums of 16 x 8 patches
     int total_units;
     int sms;
+    const char *tmaps;      // device [n_prob] tensor maps of the count planes
 };
 bool tc_supported(const Problem &h);
 int tc_units_per_problem(const Problem &h);
+// bytes of a problem's per-pass f16 delta rows
+size_t tc_delta_bytes(const Problem &h);
+// bytes of one tensor map, and its encoding for a problem's count planes (host)
+int tc_tensor_map_bytes();
+cudaError_t encode_tc_tensor_map(const Problem &h, void *out);
 cudaError_t prepare_tc();
 cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm);
-// f16 copies of the counts (tc_counts16) from the counts, every problem
-cudaError_t launch_tc_refresh(const Problem *dprob, const std::vector<Problem> &hp,
-                              cudaStream_t st);
 
 }  // namespace bn

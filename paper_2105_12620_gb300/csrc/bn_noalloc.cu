@@ -174,16 +174,26 @@ extern "C" int bn_evaluate_energy_noalloc(const int32_t *counts, int32_t n_field
     auto *scratch = static_cast<unsigned long long *>(g_scratch_ptr[dev].load());
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
+    // an error the caller left pending is reported as such (and left pending), not taken for
+    // a failure of the launches below
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return nfail(BN_ERR_CUDA, std::string("a CUDA error was pending before the call: ") +
+                                      cudaGetErrorString(e));
     const int used = n_fields * kMaxClasses;
     k_noalloc_clear<<<(used + 255) / 256, 256, 0, stream>>>(scratch, used);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return nfail(BN_ERR_CUDA, std::string("launch of the clear: ") + cudaGetErrorString(e));
     const int P = width * height;
     dim3 grid((P + kNoAllocThreads / 32 - 1) / (kNoAllocThreads / 32), n_fields);
     k_noalloc_energy<<<grid, kNoAllocThreads, 0, stream>>>(counts, width, height, n_integrands,
                                                            st, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return nfail(BN_ERR_CUDA, std::string("launch of the class sums: ") + cudaGetErrorString(e));
     k_noalloc_finalize<<<(n_fields + 63) / 64, 64, 0, stream>>>(scratch, n_fields, n_points, st,
                                                                 energy);
     note_launches(3);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return nfail(BN_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return nfail(BN_ERR_CUDA, std::string("launch of the weighted sum: ") + cudaGetErrorString(e));
     return BN_OK;
 }

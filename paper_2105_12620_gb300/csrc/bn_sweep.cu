@@ -168,19 +168,6 @@ __global__ void __launch_bounds__(kPlainThreads) k_commit_plain(const Problem *p
                 *ra = *rb;
                 *rb = t;
             }
-            if (pb.tc_counts16) {  // the f16 copy of the tensor-core schedule
-                const int nv = pb.row_bytes >> 3;  // 16-byte pieces of f16 per pixel
-                for (int vi = lane; vi < nv; vi += 32) {
-                    const size_t plane = (size_t)(vi >> 3) * pb.P;
-                    uint4 *ra = reinterpret_cast<uint4 *>(pb.tc_counts16 + ((plane + a) << 6)) +
-                                (vi & 7);
-                    uint4 *rb = reinterpret_cast<uint4 *>(pb.tc_counts16 + ((plane + b) << 6)) +
-                                (vi & 7);
-                    const uint4 t = *ra;
-                    *ra = *rb;
-                    *rb = t;
-                }
-            }
             if (lane == 0) {
                 const int t = pb.sidx[a];
                 pb.sidx[a] = pb.sidx[b];

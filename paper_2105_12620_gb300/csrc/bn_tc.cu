@@ -1,5 +1,5 @@
 // bn_tc.cu — one pass of the parallel swap optimiser (Sec. 3.4) with the stencil of Eq. 1 on the
-// fifth-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
+// fifth-generation tensor cores (tcgen05.mma; A operand and accumulators in tensor memory).
 //
 // For every proposed pixel n of a pass (one side of a valid couple) let delta_n =
 // k_partner(n) - k_n.  The class sums of a couple j = (a, b) are A_c = S_c(a) + S_c(b) with
@@ -9,32 +9,46 @@
 // (rows n).  The tile is cut into patches of 16 x 8 pixels.  Per patch the tensor core forms
 // D[q][n] for the patch's 128 pixels q (M = 128) and the proposed pixels n within the weight
 // radius of it (the patch's list, at most 160 per product), accumulating over all T integrands
-// in tensor memory; about a fifth of the entries lie inside the radius and are kept.  The f16
-// operands are exact (counts <= 64, |delta| <= 64) and the f32 sums stay within 2^24
-// (T N^2 <= 2^24 for 8-bit counts), so every kept entry is an exact integer.
+// in tensor memory; about a fifth of the entries lie inside the radius and are kept.
+//
+// Exactness.  The A operand holds the centred counts c_q = k_q - N/2 (|c| <= N/2), the B operand
+// the deltas (|delta| <= N), both exact in f16; every entry of D is an integer of magnitude at
+// most T (N/2) N <= 2^24 (checked at plan time), exact in the f32 accumulators.  The centring
+// adds (N/2) (sum_t delta_n[t]) x |S_c(n)| to S_c(n); side b carries -delta_a and on a torus
+// |S_c(a) \ b| = |S_c(b) \ a|, so the two corrections cancel in A_c.
 //
 // A pass:
-//   k_tc_lists     one warp per couple of the pass (as in the plain schedule): its class sums
-//                  cleared, its f16 delta row k_b - k_a written for every stage, and each of its
-//                  pixels appended to the list of every patch within the radius of it
-//   k_tc_stencil   one CTA per SM over the patches, warp-specialised:
-//                    9 producer warps   cp.async of whole 128-byte rows (four per warp
-//                                       instruction) of the f16 count copy (A) and of the
-//                                       delta rows (B) straight into the 128-byte swizzled
-//                                       K-major layout; stages of 64 integrands
-//                    1 MMA warp         four tcgen05.mma (K = 16 each) per stage
-//                    4 epilogue warps   tensor memory -> registers; for radius 6 a transpose
-//                                       of 32 columns through shared memory, each warp summing
-//                                       a quarter of the stencil offsets per listed pixel with
-//                                       compile-time classes; other radii a 2-D class table per
-//                                       entry; class sums to global memory (integer reductions)
-//                  five stages in a ring, two accumulator buffers in tensor memory
+//   k_tc_lists     one warp per couple: its class sums cleared, its f16 delta row k_b - k_a
+//                  written per stage of 64 integrands, each of its pixels appended to the list
+//                  of every patch within the radius
+//   k_tc_stencil   one CTA of 16 warps per SM over the patches:
+//                    A loader (1 thread)  one TMA box per 128-byte count chunk: the patch's 128
+//                                         pixels x 128 bytes (zero outside the tile), 128-byte
+//                                         swizzle, into a ring of four boxes
+//                    4 converter warps    thread = patch pixel = tensor-memory lane: its chunk
+//                                         -> exact centred f16 -> tensor memory (tcgen05.st),
+//                                         64 integrands per slot, four slots
+//                    2 producer warps     cp.async of the listed couples' delta rows (B)
+//                                         straight into the 128-byte swizzled K-major layout,
+//                                         five stages of 64 integrands
+//                    1 MMA warp           four tcgen05.mma (A from tensor memory, B from shared
+//                                         memory, K = 16) per stage into one of two
+//                                         accumulators (M = 128, N <= 160)
+//                    8 epilogue warps     16 accumulator columns per warp and step, transposed
+//                                         through shared memory 32 columns at a time; for
+//                                         radius 6 each warp owns whole distance classes and
+//                                         sums them over the stencil offsets of every listed
+//                                         pixel (compile-time offsets), then adds them to the
+//                                         couple's class sums in global memory; other radii
+//                                         and narrow tiles go through a class table and
+//                                         shared-memory atomics
 //   k_tc_finalize  change of Eq. 1 from the class sums, flags and pixel claims
-//   then the resolve and commit kernels of the plain schedule (the commit also swaps the f16
-//   copy, which k_tc_refresh rebuilds from the counts at the start of every run).
+//   then the resolve and commit kernels of the plain schedule.
 // Every wait is bounded; a wait that runs out raises the problems' error word and the CTA
 // drains its copies and products, frees its tensor memory and returns.
 #include <utility>
+
+#include <cuda.h>
 
 #include "bn_launch.h"
 #include "bn_tcgen05.cuh"
@@ -44,40 +58,47 @@ namespace {
 
 constexpr int kPW = 16, kPH = 8, kTcM = kPW * kPH;  // patch: M = 128 pixels
 constexpr int kNB = 160;                             // listed pixels per product (N)
-constexpr int kStages = 5;                           // ring of 64-integrand stages
-constexpr int kLook = 3;                             // stages in flight per producer thread
-constexpr int kAStage = kTcM * 128;                  // 16 KB: 128 rows x 64 f16
-constexpr int kBStage = kNB * 128;                   // 20 KB: 160 rows x 64 f16
-constexpr int kStageBytes = kAStage + kBStage;
-constexpr int kEpiWarps = 4, kProdWarps = (kTcM + kNB) / 32;  // eight pieces per thread
+constexpr int kABoxes = 4;                           // ring of count boxes (TMA)
+constexpr int kASlots = 4;                           // A slots of 64 integrands in tensor memory
+constexpr int kBStages = 5;                          // ring of delta stages of 64 integrands
+constexpr int kBLook = 3;                            // delta stages in flight per thread
+constexpr int kBoxBytes = kTcM * 128;                // 16 KB: 128 pixels x 128 count bytes
+constexpr int kBStageBytes = kNB * 128;              // 20 KB: 160 rows x 64 f16
+constexpr int kEpiWarps = 8, kConvWarps = 4, kProdWarps = 2;
 constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kConvWarp0 = kEpiWarps;                // converter warp c reads lane quadrant c
+constexpr int kProdWarp0 = kConvWarp0 + kConvWarps;
+constexpr int kLoadWarp = kProdWarp0 + kProdWarps;
+constexpr int kMmaWarp = kLoadWarp + 1;
+constexpr int kTcThreads = (kMmaWarp + 1) * 32;      // 512
 constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kMmaWarp = kEpiWarps + kProdWarps;
-constexpr int kTcThreads = (kMmaWarp + 1) * 32;      // 448
-constexpr uint32_t kTmemCols = 512, kTmemBuf = 256;  // two accumulator buffers
+constexpr int kBTasks = kNB * 8 / kProdThreads;      // 16-byte pieces per producer thread
+constexpr uint32_t kTmemCols = 512, kAccCols = kNB;  // accumulators at columns 0 and 160
+constexpr uint32_t kColA = 2 * kAccCols;             // A slot s at column 320 + 32 s
 constexpr int kTabMax = 65;                          // squared distances 0..64 (radius <= 8)
 constexpr long long kSpin = 1ll << 31;               // ~1 s at 2 GHz
 constexpr unsigned long long kErrTc = 3ull;
 constexpr int kFlushBatch = 5;                       // class-sum rows sent per batch
+constexpr int kTensorMapBytes = 128;                 // one CUtensorMap per problem
+static_assert(kConvWarp0 % 4 == 0, "lane quadrants of the converter warps");
+static_assert(kColA + 32 * kASlots <= kTmemCols, "tensor memory");
+static_assert(kBTasks * kProdThreads == 8 * kNB && kProdThreads == 64, "producer rows");
 
 // shared memory layout (offsets from a 1024-byte aligned base)
-// epilogue scratch: int32 [kNB][32] class sums (lane-per-pixel paths), or a 32-column transpose
-// of the accumulators, float [32][128], and per-warp partial class sums, int32 [4][32][33]
-// (column-per-thread path)
-constexpr int kOffAcc = kStages * kStageBytes;
-constexpr int kOffPart = kOffAcc + 32 * kTcM * 4;
-constexpr int kEpiScratch = kNB * 32 * 4 > 32 * kTcM * 4 + 4 * 32 * 33 * 4
-                                ? kNB * 32 * 4
-                                : 32 * kTcM * 4 + 4 * 32 * 33 * 4;
-constexpr int kOffCol = kOffAcc + kEpiScratch;        // int4 [2][kNB] per listed pixel
-constexpr int kOffTab = kOffCol + 2 * kNB * 16;       // int32 [80] class of a squared distance
-constexpr int kOffTab2 = kOffTab + 80 * 4;            // int8 [2-D offset] class (fast path)
-constexpr int kTab2Max = 1664;                        // (2 (16 + 8) + 1) x (2 (8 + 8) + 1)
-constexpr int kOffBar = kOffTab2 + kTab2Max;          // mbarriers
-constexpr int kNBars = 2 * kStages + 5;
-constexpr int kOffMisc = kOffBar + kNBars * 8;        // tensor-memory base, abort flag
+constexpr int kOffA = 0;                                    // count boxes, swizzled
+constexpr int kOffB = kOffA + kABoxes * kBoxBytes;          // delta stages, swizzled
+constexpr int kOffDt = kOffB + kBStages * kBStageBytes;     // epilogue scratch: int32 [2][32][128]
+constexpr int kDtBytes = 2 * 32 * kTcM * 4;                 //   transposes, or int32 [kNB][32]
+constexpr int kOffCol = kOffDt + kDtBytes;                  //   class sums of the table paths
+constexpr int kOffTab = kOffCol + 2 * 2 * kNB * 16;         // int32 [80] class of a squared distance
+constexpr int kOffTab2 = kOffTab + 80 * 4;                  // int8 [2-D offset] class (table path)
+constexpr int kTab2Max = 1664;                              // (2 (16 + 8) + 1) x (2 (8 + 8) + 1)
+constexpr int kOffBar = kOffTab2 + kTab2Max;                // mbarriers
+constexpr int kNBars = 2 * kABoxes + 2 * kASlots + 2 * kBStages + 4 + 1;
+constexpr int kOffMisc = kOffBar + kNBars * 8;              // tensor-memory base, abort flags
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;
-static_assert(kStageBytes % 1024 == 0 && kAStage % 1024 == 0, "stage alignment");
+static_assert(kNB * 32 * 4 <= kDtBytes, "class sums of the table paths");
+static_assert(kOffB % 1024 == 0 && kBStageBytes % 1024 == 0 && kOffDt % 16 == 0, "alignment");
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
@@ -86,6 +107,7 @@ struct TcArgs {
     int n_prob;
     const int *unit_start;  // [n_prob + 1] prefix sums of patches
     int total_units;
+    const char *tmaps;      // [n_prob] tensor maps of the count planes (kTensorMapBytes each)
 };
 
 // ---- PTX helpers ----------------------------------------------------------------------------
@@ -97,6 +119,12 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
@@ -125,6 +153,12 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
         }
     }
 }
+// the same for a whole warp: true only if every lane's wait succeeded
+__device__ __forceinline__ bool tc_wait_warp(uint64_t *bar, uint32_t parity,
+                                             volatile int *abort_flag)
+{
+    return __all_sync(0xFFFFFFFFu, tc_wait(bar, parity, abort_flag));
+}
 // integer add to global memory without a return value
 __device__ __forceinline__ void red_add_global(int32_t *p, int v)
 {
@@ -145,6 +179,16 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait()
 {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// 4-D tiled TMA load into shared memory, completion counted in bytes on *bar
+__device__ __forceinline__ void tma_load_4d(void *dst, const char *tmap, int c0, int c1, int c2,
+                                            int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(tc::saddr(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::saddr(bar))
+        : "memory");
 }
 // named barrier of the epilogue warps
 __device__ __forceinline__ void epi_sync()
@@ -177,29 +221,36 @@ __device__ __forceinline__ int find_problem(const int *start, int n, int u)
     return lo;
 }
 
-// four bytes -> two f16x2 (bytes 0,1 and 2,3); the bytes are read as 1024 + byte and 1024 is
-// subtracted, so the values are exact
+// f16x2 of an unsigned 16-bit pair below 1024: each half read as 1024 + value (exact)
+constexpr uint32_t kH2Magic = 0x64006400u;
+__device__ __forceinline__ uint32_t h2_sub(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// four bytes -> two f16x2 (bytes 0,1 and 2,3), each byte read as 1024 + byte; bias2 is
+// subtracted, so the values (byte + 1024 - bias) are exact
 __device__ __forceinline__ void bytes_to_h2(uint32_t x, uint32_t bias2, uint32_t &lo, uint32_t &hi)
 {
-    const uint32_t a = __byte_perm(x, 0x64646464u, 0x4140);
-    const uint32_t b = __byte_perm(x, 0x64646464u, 0x4342);
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(a), "r"(bias2));
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(b), "r"(bias2));
+    lo = h2_sub(__byte_perm(x, 0x64646464u, 0x4140), bias2);
+    hi = h2_sub(__byte_perm(x, 0x64646464u, 0x4342), bias2);
 }
-constexpr uint32_t kBiasCount = 0x64006400u;  // f16x2 (1024, 1024)
 // four byte differences a - b -> two f16x2: both read as 1024 + byte, then subtracted
 __device__ __forceinline__ void bytes_sub_h2(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi)
 {
-    const uint32_t a0 = __byte_perm(a, 0x64646464u, 0x4140);
-    const uint32_t a1 = __byte_perm(a, 0x64646464u, 0x4342);
-    const uint32_t b0 = __byte_perm(b, 0x64646464u, 0x4140);
-    const uint32_t b1 = __byte_perm(b, 0x64646464u, 0x4342);
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(a0), "r"(b0));
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(a1), "r"(b1));
+    lo = h2_sub(__byte_perm(a, 0x64646464u, 0x4140), __byte_perm(b, 0x64646464u, 0x4140));
+    hi = h2_sub(__byte_perm(a, 0x64646464u, 0x4342), __byte_perm(b, 0x64646464u, 0x4342));
 }
 
-// The unit decode shared by the three roles: the same global sequence of patches and of
-// products (jobs) on every role, from values that do not change during the launch.
+// stages of 64 integrands of a problem's count rows
+__host__ __device__ __forceinline__ int tc_stages(const Problem &pb)
+{
+    return pb.row_bytes / (64 * pb.count_bytes);
+}
+
+// The unit decode shared by the roles: the same global sequence of patches and of products on
+// every role, from values that do not change during the launch.
 struct Unit {
     const Problem *pb;
     int pid, cnt, x0, y0;
@@ -223,13 +274,13 @@ __device__ __forceinline__ Unit decode_unit(const TcArgs &args, int u, int &pi)
     return d;
 }
 
-// 2-D class table of the epilogue's fast path: offsets (dx, dy) from a proposed pixel to a patch
-// pixel, |dx| <= 16 + r, |dy| <= 8 + r, row-major with row length 2 (16 + r) + 1
+// 2-D class table of the epilogue's table path: offsets (dx, dy) from a proposed pixel to a
+// patch pixel, |dx| <= 16 + r, |dy| <= 8 + r, row-major with row length 2 (16 + r) + 1
 __host__ __device__ __forceinline__ int tab2_dx(int r) { return 16 + r; }
 __host__ __device__ __forceinline__ int tab2_dy(int r) { return 8 + r; }
 __host__ __device__ __forceinline__ int tab2_w(int r) { return 2 * (16 + r) + 1; }
-// the fast path holds when the torus is wide enough that a proposed pixel's offset from the patch
-// centre, taken as the min-image, is its true offset (below half a side): W > 2 (8 + r),
+// the table path holds when the torus is wide enough that a proposed pixel's offset from the
+// patch centre, taken as the min-image, is its true offset (below half a side): W > 2 (8 + r),
 // H > 2 (4 + r)
 __host__ __device__ __forceinline__ bool tab2_ok(int W, int H, int r)
 {
@@ -239,7 +290,7 @@ __host__ __device__ __forceinline__ bool tab2_ok(int W, int H, int r)
 // ---- compile-time stencil of radius 6: offsets with 0 < dx^2 + dy^2 <= 36, by class ----------
 struct Stencil6 {
     int n = 0, ncls = 0;
-    int dx[169] = {}, dy[169] = {}, cls[169] = {}, d2[32] = {};
+    int dx[169] = {}, dy[169] = {}, cls[169] = {}, d2[32] = {}, mult[32] = {};
     constexpr Stencil6()
     {
         for (int dd = 1; dd <= 36; ++dd) {
@@ -250,6 +301,7 @@ struct Stencil6 {
                         dx[n] = x;
                         dy[n] = y;
                         cls[n] = ncls;
+                        ++mult[ncls];
                         ++n;
                         any = true;
                     }
@@ -258,40 +310,114 @@ struct Stencil6 {
     }
 };
 constexpr Stencil6 kSt6{};
-constexpr int kCls6 = 18, kOffPerWarp = 28;
-static_assert(kSt6.n == 4 * kOffPerWarp && kSt6.ncls == kCls6, "radius-6 stencil");
+constexpr int kCls6 = 18;
+static_assert(kSt6.n == 112 && kSt6.ncls == kCls6, "radius-6 stencil");
 
-// one offset of the radius-6 stencil: the accumulator row of patch pixel p + offset, if that
-// pixel is in the patch and is not the partner, added to its class sum
-template <int O>
-__device__ __forceinline__ void stencil_add(const float *dtc, int plx, int ply, int plane,
-                                            int lane, int (&a)[kCls6])
+// The 18 classes split over the 8 epilogue warps (largest multiplicity first, each to the warp
+// with the fewest offsets so far): every warp owns whole classes, at most 16 offsets.
+constexpr int kGrpMaxOff = 16, kGrpMaxCls = 4;
+struct Groups6 {
+    int n[kEpiWarps] = {}, ncls[kEpiWarps] = {};
+    int cls[kEpiWarps][kGrpMaxCls] = {};
+    int dx[kEpiWarps][kGrpMaxOff] = {}, dy[kEpiWarps][kGrpMaxOff] = {},
+        k[kEpiWarps][kGrpMaxOff] = {};
+    constexpr Groups6()
+    {
+        int load[kEpiWarps] = {}, owner[kCls6] = {};
+        bool used[kCls6] = {};
+        for (int it = 0; it < kCls6; ++it) {
+            int best = 0, bm = -1;
+            for (int c = 0; c < kCls6; ++c)
+                if (!used[c] && kSt6.mult[c] > bm) {
+                    bm = kSt6.mult[c];
+                    best = c;
+                }
+            used[best] = true;
+            int b = 0;
+            for (int i = 1; i < kEpiWarps; ++i)
+                if (load[i] < load[b]) b = i;
+            load[b] += bm;
+            owner[best] = b;
+            cls[b][ncls[b]++] = best;
+        }
+        for (int o = 0; o < kSt6.n; ++o) {
+            const int c = kSt6.cls[o], b = owner[c];
+            int kk = 0;
+            for (int t = 0; t < ncls[b]; ++t)
+                if (cls[b][t] == c) kk = t;
+            dx[b][n[b]] = kSt6.dx[o];
+            dy[b][n[b]] = kSt6.dy[o];
+            k[b][n[b]] = kk;
+            ++n[b];
+        }
+    }
+    constexpr int max_n() const
+    {
+        int m = 0;
+        for (int i = 0; i < kEpiWarps; ++i) m = n[i] > m ? n[i] : m;
+        return m;
+    }
+    constexpr int max_cls() const
+    {
+        int m = 0;
+        for (int i = 0; i < kEpiWarps; ++i) m = ncls[i] > m ? ncls[i] : m;
+        return m;
+    }
+};
+constexpr Groups6 kG6{};
+static_assert(kG6.max_n() <= kGrpMaxOff && kG6.max_cls() <= kGrpMaxCls, "class groups");
+
+// one offset of warp E's classes: the transposed accumulator row of patch pixel p + offset, if
+// that pixel is in the patch and is not the partner, added to its class sum
+template <int E, int I>
+__device__ __forceinline__ void g6_add(const int32_t *dtc, int plx, int ply, int plane, int lane,
+                                       int (&a)[kGrpMaxCls])
 {
-    constexpr int dx = kSt6.dx[O], dy = kSt6.dy[O], c = kSt6.cls[O];
-    const int lx = plx + dx, ly = ply + dy;
-    const int q = ly * kPW + lx;
-    const bool in = (unsigned)lx < (unsigned)kPW && (unsigned)ly < (unsigned)kPH && q != plane;
-    // unconditional load; a lane outside the patch reads its own bank (row lane of its column)
-    const float x = dtc[in ? q : lane];
-    a[c] += in ? __float2int_rn(x) : 0;  // an exact integer held in f32
+    if constexpr (I < kG6.n[E]) {
+        constexpr int dx = kG6.dx[E][I], dy = kG6.dy[E][I], k = kG6.k[E][I];
+        const int lx = plx + dx, ly = ply + dy;
+        const int q = ly * kPW + lx;
+        const bool in = (unsigned)lx < (unsigned)kPW && (unsigned)ly < (unsigned)kPH && q != plane;
+        // unconditional load; a lane outside the patch reads its own bank (row lane)
+        const int x = dtc[in ? q : lane];
+        a[k] += in ? x : 0;
+    }
 }
-template <int Q, int... I>
-__device__ __forceinline__ void stencil_quarter(const float *dtc, int plx, int ply, int plane,
-                                                int lane, int (&a)[kCls6],
-                                                std::integer_sequence<int, I...>)
+// warp E's class K of the listed pixel sent to the couple's class sums (the b side carries
+// -delta)
+template <int E, int K>
+__device__ __forceinline__ void g6_send(const int (&a)[kGrpMaxCls], int32_t *side, int slot)
 {
-    (stencil_add<Q * kOffPerWarp + I>(dtc, plx, ply, plane, lane, a), ...);
+    if constexpr (K < kG6.ncls[E]) {
+        constexpr int c = kG6.cls[E][K];
+        if (a[K]) red_add_global(side + (size_t)slot * kMaxClasses + c, (slot & 1) ? -a[K] : a[K]);
+    }
 }
-// warp w's quarter of the stencil offsets
-__device__ __forceinline__ void stencil_warp(int w, const float *dtc, int4 c1, int lane,
-                                             int (&a)[kCls6])
+template <int E, int... I>
+__device__ __forceinline__ void g6_sum(const int32_t *dtc, int4 c1, int lane, int32_t *side,
+                                       std::integer_sequence<int, I...>)
 {
-    using Seq = std::make_integer_sequence<int, kOffPerWarp>;
+    int a[kGrpMaxCls] = {0, 0, 0, 0};
+    (g6_add<E, I>(dtc, c1.x, c1.y, c1.z, lane, a), ...);
+    g6_send<E, 0>(a, side, c1.w);
+    g6_send<E, 1>(a, side, c1.w);
+    g6_send<E, 2>(a, side, c1.w);
+    g6_send<E, 3>(a, side, c1.w);
+}
+// warp w's classes for the listed pixel of this lane
+__device__ __forceinline__ void g6_warp(int w, const int32_t *dtc, int4 c1, int lane,
+                                        int32_t *side)
+{
+    using Seq = std::make_integer_sequence<int, kGrpMaxOff>;
     switch (w) {
-    case 0: stencil_quarter<0>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-    case 1: stencil_quarter<1>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-    case 2: stencil_quarter<2>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
-    default: stencil_quarter<3>(dtc, c1.x, c1.y, c1.z, lane, a, Seq{}); break;
+    case 0: g6_sum<0>(dtc, c1, lane, side, Seq{}); break;
+    case 1: g6_sum<1>(dtc, c1, lane, side, Seq{}); break;
+    case 2: g6_sum<2>(dtc, c1, lane, side, Seq{}); break;
+    case 3: g6_sum<3>(dtc, c1, lane, side, Seq{}); break;
+    case 4: g6_sum<4>(dtc, c1, lane, side, Seq{}); break;
+    case 5: g6_sum<5>(dtc, c1, lane, side, Seq{}); break;
+    case 6: g6_sum<6>(dtc, c1, lane, side, Seq{}); break;
+    default: g6_sum<7>(dtc, c1, lane, side, Seq{}); break;
     }
 }
 
@@ -306,52 +432,140 @@ __device__ __forceinline__ bool classes_match6(const int32_t *d2, std::integer_s
     return ((d2[C] == D2Of6<C>::v) && ...);
 }
 
-// ---- producer warps -----------------------------------------------------------------------
-// A stage holds 128 A rows (the patch pixels' f16 counts) and up to kNB B rows (the listed
-// couples' f16 deltas) of 64 integrands, each row eight 16-byte pieces, copied by cp.async
-// straight into the swizzled slots (piece j of row r in slot j ^ (r mod 8)).  Producer thread pt
-// owns the pieces pt + kProdThreads k, k < kTasks: a warp copies four whole 128-byte rows per
-// instruction.  A rows of pixels outside a ragged tile are written as zeros.
-constexpr int kTasks = 8;
-static_assert(kTasks * kProdThreads == 8 * (kTcM + kNB), "one piece per task");
-static_assert(kProdThreads % 8 == 0, "the piece index is the same for all of a thread's tasks");
-
-// row kinds of a producer task
-enum : int { kRowNone = 0, kRowCount = 1, kRowDelta = 2, kRowZero = 3 };
-
-// make this thread's copies (and zero stores) of stage gi visible to the tensor core, then one
-// arrival per warp
-__device__ __forceinline__ void publish(char *smem, uint64_t *full, uint32_t gi, uint32_t kinds,
-                                        const uint32_t (&roff)[kTasks], int piece)
+// ---- A loader (one thread) -------------------------------------------------------------------
+// For every product, one TMA box per 128-byte count chunk: the patch's 16 x 8 pixels x 128
+// bytes (8-bit counts: 128 integrands; 16-bit: 64), zero outside the tile.
+__device__ void tc_load_a(const TcArgs &args, char *smem, uint64_t *a_full, uint64_t *a_empty,
+                          volatile int *abort_flag, volatile int *no_abort)
 {
-    char *st = smem + (gi % kStages) * kStageBytes;
-#pragma unroll
-    for (int k = 0; k < kTasks; ++k)
-        if (((kinds >> (2 * k)) & 3u) == (uint32_t)kRowZero)
-            reinterpret_cast<uint4 *>(st + roff[k])[piece ^ ((roff[k] >> 7) & 7u)] =
-                make_uint4(0u, 0u, 0u, 0u);
-    tc::fence_async_smem();
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&full[gi % kStages]);
+    uint32_t g = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+        int pi;
+        const Unit d = decode_unit(args, u, pi);
+        if (d.cnt <= 0) continue;
+        const int nbox = d.pb->row_bytes >> 7;
+        const char *tmap = args.tmaps + (size_t)pi * kTensorMapBytes;
+        for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB)
+            for (int c = 0; c < nbox; ++c) {
+                const uint32_t slot = g % kABoxes, use = g / kABoxes;
+                if (!tc_wait(&a_empty[slot], (use & 1u) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&a_full[slot], kBoxBytes);
+                tma_load_4d(smem + kOffA + slot * kBoxBytes, tmap, 0, d.x0, d.y0, c,
+                            &a_full[slot]);
+                ++g;
+            }
+    }
+    // every box issued has landed before the CTA leaves (each slot's last box completes its
+    // phase; a box already consumed has completed it long ago)
+    for (uint32_t k = 0; k < (uint32_t)kABoxes && k < g; ++k) {
+        const uint32_t gl = g - 1u - k;
+        tc_wait(&a_full[gl % kABoxes], (gl / kABoxes) & 1u, no_abort);
+    }
 }
 
-__device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint64_t *empty,
+// ---- converter warps ---------------------------------------------------------------------------
+// Thread = patch pixel = tensor-memory lane (warp c of the group owns lane quadrant c): reads its
+// row of the box (128 bytes), converts it to centred f16 and stores 64 integrands per slot.
+__device__ void tc_convert(const TcArgs &args, char *smem, uint64_t *a_full, uint64_t *a_empty,
+                           uint64_t *s_full, uint64_t *s_empty, uint32_t tmem,
                            volatile int *abort_flag)
 {
-    const int pt = threadIdx.x - kEpiThreads;
-    const int piece = pt & 7;
-    constexpr int kRowStep = kProdThreads / 8;  // rows between a thread's tasks
-    uint32_t roff[kTasks];
+    const int ct = threadIdx.x - kConvWarp0 * 32;  // 0 .. 127
+    const int lane = ct & 31;
+    const int lx = ct & 15, ly = ct >> 4;
+    const uint32_t lane_base = (uint32_t)(ct & ~31) << 16;
+    uint32_t gb = 0, gs = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+        int pi;
+        const Unit d = decode_unit(args, u, pi);
+        if (d.cnt <= 0) continue;
+        const Problem &pb = *d.pb;
+        const bool qin = d.x0 + lx < pb.W && d.y0 + ly < pb.H;
+        const int nbox = pb.row_bytes >> 7;
+        const bool wide = pb.count_bytes == 2;
+        // 1024 + k - (1024 + N/2) = k - N/2, exact
+        const uint32_t hb = 0x6400u + (uint32_t)(pb.N >> 1);
+        const uint32_t bias = hb | (hb << 16);
+        for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB)
+            for (int c = 0; c < nbox; ++c) {
+                const uint32_t slot = gb % kABoxes, use = gb / kABoxes;
+                if (!tc_wait_warp(&a_full[slot], use & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const char *row = smem + kOffA + slot * kBoxBytes + ct * 128;
+                uint4 w[8];
 #pragma unroll
-    for (int k = 0; k < kTasks; ++k) {
-        const int row = (pt >> 3) + kRowStep * k, n = row - kTcM;
-        roff[k] = row < kTcM ? (uint32_t)((row >> 3) * 1024 + (row & 7) * 128)
-                             : (uint32_t)(kAStage + (n >> 3) * 1024 + (n & 7) * 128);
+                for (int j = 0; j < 8; ++j)
+                    w[j] = *reinterpret_cast<const uint4 *>(row + ((j ^ (ct & 7)) << 4));
+                const int nsub = wide ? 1 : 2;
+                for (int sb = 0; sb < nsub; ++sb) {
+                    const uint32_t as = gs % kASlots, ause = gs / kASlots;
+                    if (!tc_wait_warp(&s_empty[as], (ause & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    uint32_t o[32];
+                    if (wide) {  // 64 integrands of 16 bits: one f16x2 per word
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            o[4 * j + 0] = h2_sub(w[j].x | kH2Magic, bias);
+                            o[4 * j + 1] = h2_sub(w[j].y | kH2Magic, bias);
+                            o[4 * j + 2] = h2_sub(w[j].z | kH2Magic, bias);
+                            o[4 * j + 3] = h2_sub(w[j].w | kH2Magic, bias);
+                        }
+                    } else {  // bytes 64 sb .. 64 sb + 63: two f16x2 per word
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint4 x = sb ? w[4 + j] : w[j];
+                            bytes_to_h2(x.x, bias, o[8 * j + 0], o[8 * j + 1]);
+                            bytes_to_h2(x.y, bias, o[8 * j + 2], o[8 * j + 3]);
+                            bytes_to_h2(x.z, bias, o[8 * j + 4], o[8 * j + 5]);
+                            bytes_to_h2(x.w, bias, o[8 * j + 6], o[8 * j + 7]);
+                        }
+                    }
+                    if (!qin) {  // pixels outside a ragged tile: zero rows
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) o[i] = 0u;
+                    }
+                    tc::tmem_st32(tmem + lane_base + kColA + 32u * as, o);
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&s_full[as]);
+                    ++gs;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&a_empty[slot]);
+                if (!ok) break;
+                ++gb;
+            }
     }
-    const uint32_t sbase = tc::saddr(smem);
-    uint32_t kh[kLook];  // packed task kinds of the stages 1 .. kLook back
-#pragma unroll
-    for (int b = 0; b < kLook; ++b) kh[b] = 0u;
+}
+
+// ---- producer warps (B) ------------------------------------------------------------------------
+// A stage holds up to kNB delta rows of 64 integrands, each row eight 16-byte pieces, copied by
+// cp.async straight into the swizzled slots (piece j of row r in slot j ^ (r mod 8)).  Producer
+// thread pt owns piece pt mod 8 of rows pt / 8 + 8 k: a warp copies four whole rows per
+// instruction.
+__device__ __forceinline__ void publish_b(uint64_t *b_full, uint32_t gi)
+{
+    tc::fence_async_smem();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&b_full[gi % kBStages]);
+}
+
+__device__ void tc_produce_b(const TcArgs &args, char *smem, uint64_t *b_full, uint64_t *b_empty,
+                             volatile int *abort_flag)
+{
+    const int pt = threadIdx.x - kProdWarp0 * 32;  // 0 .. 63
+    const int piece = pt & 7, r0 = pt >> 3;          // rows r0 + 8 k: r mod 8 = r0, r / 8 = k
+    const uint32_t dpos = tc::saddr(smem + kOffB) + (uint32_t)(r0 * 128 + ((piece ^ r0) << 4));
     uint32_t g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
@@ -359,113 +573,92 @@ __device__ void tc_produce(const TcArgs &args, char *smem, uint64_t *full, uint6
         const Unit d = decode_unit(args, u, pi);
         if (d.cnt <= 0) continue;
         const Problem &pb = *d.pb;
-        const int nks = pb.row_bytes >> 6;
-        const uint16_t *const cnt16 = pb.tc_counts16 + 8 * piece;
-        const uint16_t *const del16 = pb.tc_delta16 + 8 * piece;
-        const size_t cplane = (size_t)pb.P << 6, dplane = (size_t)pb.M << 6;  // f16 per stage
+        const int kst = tc_stages(pb);
+        const uint16_t *const del = pb.tc_delta16 + 8 * piece;
+        const size_t dplane = (size_t)pb.M << 6;  // f16 per stage
         const int4 *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
-            uint32_t kinds = 0u;
-            int idx[kTasks];  // pixel (A) or couple (B) of each task
+            int idx[kBTasks];  // couple of each task's row (rows nn .. kNB - 1 stay unloaded:
+                               // they feed columns the epilogue ignores)
 #pragma unroll
-            for (int k = 0; k < kTasks; ++k) {
-                int kind = kRowNone;
-                idx[k] = 0;
-                const int row = (pt >> 3) + kRowStep * k;
-                if (row < kTcM) {
-                    const int qx = d.x0 + (row & 15), qy = d.y0 + (row >> 4);
-                    if (qx < pb.W && qy < pb.H) {
-                        kind = kRowCount;
-                        idx[k] = qy * pb.W + qx;
-                    } else {
-                        kind = kRowZero;
-                    }
-                } else if (row - kTcM < nn) {  // rows nn .. npad - 1 feed ignored columns
-                    kind = kRowDelta;
-                    idx[k] = list[n0 + row - kTcM].z >> 1;  // couple of the listed slot
-                }
-                kinds |= (uint32_t)kind << (2 * k);
+            for (int k = 0; k < kBTasks; ++k) {
+                const int row = r0 + 8 * k;
+                idx[k] = row < nn ? (list[n0 + row].z >> 1) : -1;
             }
-            for (int ks = 0; ks < nks; ++ks) {
-                const uint32_t slot = g % kStages, use = g / kStages;
-                if (!tc_wait(&empty[slot], (use & 1u) ^ 1u, abort_flag)) {
+            for (int ks = 0; ks < kst; ++ks) {
+                const uint32_t slot = g % kBStages, use = g / kBStages;
+                if (!tc_wait_warp(&b_empty[slot], (use & 1u) ^ 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
-                const uint32_t st = sbase + slot * kStageBytes;
-                const uint16_t *ca = cnt16 + (size_t)ks * cplane;
-                const uint16_t *cd = del16 + (size_t)ks * dplane;
+                const uint32_t st = dpos + slot * kBStageBytes;
+                const uint16_t *cd = del + (size_t)ks * dplane;
 #pragma unroll
-                for (int k = 0; k < kTasks; ++k) {
-                    const uint32_t kind = (kinds >> (2 * k)) & 3u;
-                    const uint32_t dst = st + roff[k] + ((piece ^ ((roff[k] >> 7) & 7u)) << 4);
-                    if (kind == (uint32_t)kRowCount) cp_async16(dst, ca + ((size_t)idx[k] << 6));
-                    if (kind == (uint32_t)kRowDelta) cp_async16(dst, cd + ((size_t)idx[k] << 6));
-                }
+                for (int k = 0; k < kBTasks; ++k)
+                    if (idx[k] >= 0) cp_async16(st + k * 1024, cd + ((size_t)idx[k] << 6));
                 cp_async_commit();
-                if (g >= (uint32_t)kLook) {
-                    cp_async_wait<kLook>();
-                    publish(smem, full, g - kLook, kh[kLook - 1], roff, piece);
+                if (g >= (uint32_t)kBLook) {
+                    cp_async_wait<kBLook>();
+                    publish_b(b_full, g - kBLook);
                 }
-#pragma unroll
-                for (int b = kLook - 1; b > 0; --b) kh[b] = kh[b - 1];
-                kh[0] = kinds;
                 ++g;
             }
         }
     }
     cp_async_wait<0>();
-    if (ok) {  // the last kLook stages, oldest first
-#pragma unroll
-        for (int b = kLook - 1; b >= 0; --b)
-            if (g >= (uint32_t)(b + 1))
-                publish(smem, full, g - (uint32_t)(b + 1), kh[b], roff, piece);
+    if (ok) {  // the last kBLook stages, oldest first
+        for (uint32_t b = kBLook; b >= 1; --b)
+            if (g >= b) publish_b(b_full, g - b);
     }
 }
 
-// ---- MMA warp -------------------------------------------------------------------------------
-__device__ void tc_mma(const TcArgs &args, char *smem, uint64_t *full, uint64_t *empty,
-                       uint64_t *tfull, uint64_t *tempty, uint64_t *done, uint32_t tmem,
+// ---- MMA warp ----------------------------------------------------------------------------------
+__device__ void tc_mma(const TcArgs &args, char *smem, uint64_t *s_full, uint64_t *s_empty,
+                       uint64_t *b_full, uint64_t *b_empty, uint64_t *acc_full,
+                       uint64_t *acc_empty, uint64_t *done, uint32_t tmem,
                        volatile int *abort_flag, volatile int *no_abort)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t sbase = tc::saddr(smem);
+    const uint32_t sbase = tc::saddr(smem + kOffB);
     uint32_t g = 0, jb = 0;
     bool ok = true, issued = false;
     for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
         int pi;
         const Unit d = decode_unit(args, u, pi);
         if (d.cnt <= 0) continue;
-        const int nks = d.pb->row_bytes >> 6;
+        const int kst = tc_stages(*d.pb);
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
             const uint32_t buf = jb & 1u;
-            ok = __all_sync(0xFFFFFFFFu, tc_wait(&tempty[buf], ((jb >> 1) & 1u) ^ 1u, abort_flag));
+            ok = tc_wait_warp(&acc_empty[buf], ((jb >> 1) & 1u) ^ 1u, abort_flag);
             if (!ok) break;
             tc::fence_after_sync();
-            const uint32_t dt = tmem + buf * kTmemBuf;
+            const uint32_t dt = tmem + buf * kAccCols;
             const uint32_t idesc = tc::idesc_f16_f32(kTcM, npad);
-            for (int ks = 0; ks < nks; ++ks) {
-                const uint32_t slot = g % kStages, use = g / kStages;
-                ok = __all_sync(0xFFFFFFFFu, tc_wait(&full[slot], use & 1u, abort_flag));
+            for (int ks = 0; ks < kst; ++ks) {
+                const uint32_t as = g % kASlots, bs = g % kBStages;
+                ok = tc_wait_warp(&s_full[as], (g / kASlots) & 1u, abort_flag) &&
+                     tc_wait_warp(&b_full[bs], (g / kBStages) & 1u, abort_flag);
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (lane == 0) {
-                    const uint32_t a0 = sbase + slot * kStageBytes, b0 = a0 + kAStage;
+                    const uint32_t b0 = sbase + bs * kBStageBytes;
+                    const uint32_t a0 = tmem + kColA + 32u * as;
 #pragma unroll
                     for (int k16 = 0; k16 < 4; ++k16)
-                        tc::mma_f16(dt, tc::sw128_desc(a0, k16), tc::sw128_desc(b0, k16), idesc,
-                                    (ks | k16) != 0);
-                    tc::mma_commit(&empty[slot]);
+                        tc::mma_f16_ts(dt, a0 + 8u * k16, tc::sw128_desc(b0, k16), idesc,
+                                       (ks | k16) != 0);
+                    tc::mma_commit(&b_empty[bs]);
+                    tc::mma_commit(&s_empty[as]);
                 }
                 __syncwarp();
                 issued = true;
                 ++g;
             }
             if (!ok) break;
-            if (lane == 0) tc::mma_commit(&tfull[buf]);
+            if (lane == 0) tc::mma_commit(&acc_full[buf]);
             __syncwarp();
             ++jb;
         }
@@ -478,36 +671,41 @@ __device__ void tc_mma(const TcArgs &args, char *smem, uint64_t *full, uint64_t 
     }
 }
 
-// ---- epilogue warps -------------------------------------------------------------------------
-__device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uint64_t *tempty,
-                            uint32_t tmem, volatile int *abort_flag)
+// ---- epilogue warps ----------------------------------------------------------------------------
+// Warp w reads lane quadrant w mod 4 (patch pixels 32 (w mod 4) ..) and columns 16 (w / 4) ..
+// of every 32-column step.
+__device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
+                            uint64_t *acc_empty, uint32_t tmem, volatile int *abort_flag)
 {
-    const int et = threadIdx.x;  // 0 .. 127: tensor-memory lane = patch pixel
-    const int w = et >> 5;
-    int32_t *acc = reinterpret_cast<int32_t *>(smem + kOffAcc);
-    float *dt = reinterpret_cast<float *>(smem + kOffAcc);         // [32][128], column path
-    int32_t *part = reinterpret_cast<int32_t *>(smem + kOffPart);  // [4][32][33], column path
-    // per listed pixel: (table offset, partner, slot, x | y << 16) and, for the column path,
-    // (its patch-local x, y, the partner's patch pixel or -1)
-    int4 *col = reinterpret_cast<int4 *>(smem + kOffCol);
-    int4 *col1 = col + kNB;
+    const int et = threadIdx.x;  // 0 .. 255
+    const int w = et >> 5, lane = et & 31;
+    const int quad = w & 3, half = w >> 2;
+    int32_t *dt = reinterpret_cast<int32_t *>(smem + kOffDt);  // [2][32][128] or [kNB][32]
+    // per listed pixel, by product parity: (table offset, partner, slot, x | y << 16) and
+    // (its patch-local x, y, the partner's patch pixel or -1, slot)
+    int4 *colb = reinterpret_cast<int4 *>(smem + kOffCol);
+    int4 *col1b = colb + 2 * kNB;
     int32_t *tab = reinterpret_cast<int32_t *>(smem + kOffTab);
     int8_t *tab2 = reinterpret_cast<int8_t *>(smem + kOffTab2);
-    uint32_t jb = 0;
+    const int row = 32 * quad + lane;  // the patch pixel of this thread's accumulator lane
+    const int lx = row & 15, ly = row >> 4;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+    uint32_t jb = 0, ci = 0;
     int cur = -1;
     bool ok = true;
     for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
         int pi;
         const Unit d = decode_unit(args, u, pi);
+        if (d.cnt <= 0) continue;
         const Problem &pb = *d.pb;
         const int W = pb.W, H = pb.H, hw = W >> 1, hh = H >> 1;
         const int r = pb.radius, r2 = r * r, ncls = pb.n_cls;
         const bool fast = tab2_ok(W, H, r);
         const int tw = tab2_w(r);
-        // column-per-thread path: radius 6 with the classes of the static stencil
+        // compile-time path: radius 6 with the classes of the static stencil
         const bool colpath = fast && r == 6 && ncls == kCls6 &&
                              classes_match6(pb.d2, std::make_integer_sequence<int, kCls6>{});
-        if (d.cnt > 0 && pi != cur) {  // class of each squared distance / offset of this problem
+        if (pi != cur) {  // class of each squared distance / offset of this problem
             epi_sync();
             for (int i = et; i < kTabMax; i += kEpiThreads) tab[i] = -1;
             epi_sync();
@@ -524,7 +722,6 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
             }
             cur = pi;
         }
-        const int lx = et & 15, ly = et >> 4;
         const int qx = d.x0 + lx, qy = d.y0 + ly;
         const bool qin = qx < W && qy < H;
         const int qpix = qy * W + qx;
@@ -536,125 +733,107 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *tfull, uin
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
             const uint32_t buf = jb & 1u;
+            int4 *col = colb + (jb & 1u) * kNB, *col1 = col1b + (jb & 1u) * kNB;
+            // the table paths reuse the scratch every product: the previous readers are done
+            if (!colpath) epi_sync();
             for (int n = et; n < nn; n += kEpiThreads) {
                 const int4 e = list[n0 + n];
                 const int rx = (int)(int16_t)(e.w & 0xFFFF), ry = e.w >> 16;
                 col[n] = make_int4(ry * tw + rx, e.y, e.z, (e.x % W) | ((e.x / W) << 16));
                 const int ax = e.y % W - d.x0, ay = e.y / W - d.y0;
                 const int plane = (ax >= 0 && ax < kPW && ay >= 0 && ay < kPH) ? ay * kPW + ax : -1;
-                col1[n] = make_int4(rx + kPW / 2, ry + kPH / 2, plane, 0);
+                col1[n] = make_int4(rx + kPW / 2, ry + kPH / 2, plane, e.z);
             }
-            if (!colpath)
+            if (!colpath) {
                 for (int e = et; e < nn * 8; e += kEpiThreads)
-                    reinterpret_cast<int4 *>(acc)[e] = make_int4(0, 0, 0, 0);
-            epi_sync();
-            const bool wok = tc_wait(&tfull[buf], (jb >> 1) & 1u, abort_flag);
+                    reinterpret_cast<int4 *>(dt)[e] = make_int4(0, 0, 0, 0);
+                epi_sync();
+            }
+            const bool wok = tc_wait(&acc_full[buf], (jb >> 1) & 1u, abort_flag);
             if (epi_any(!wok)) {
                 ok = false;
                 break;
             }
             tc::fence_after_sync();
-            for (int c0 = 0; c0 < npad; c0 += 32) {
-                uint32_t v[32];
-                tc::tmem_ld32(tmem + buf * kTmemBuf + (uint32_t)c0 + ((uint32_t)(w * 32) << 16),
-                              v);
+            const int nch = (npad + 31) >> 5;
+            for (int k = 0; k < nch; ++k) {
+                const int c0 = 32 * k, cc = c0 + 16 * half;  // this warp's first column
+                const bool have = cc < npad;                 // uniform per warp
+                uint32_t v[16];
+                if (have) tc::tmem_ld16(tmem + lane_base + buf * kAccCols + (uint32_t)cc, v);
+                if (k == nch - 1) {  // the accumulator is free once every lane has read it
+                    tc::fence_before_sync();
+                    mbar_arrive(&acc_empty[buf]);
+                }
                 if (colpath) {
-                    // transpose 32 columns through shared memory; warp w then sums, for the
-                    // column of each lane, its quarter of the 112 stencil offsets
-                    const int lane = et & 31;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) dt[i * kTcM + et] = __uint_as_float(v[i]);
-                    epi_sync();
-                    int a[kCls6];
-#pragma unroll
-                    for (int c = 0; c < kCls6; ++c) a[c] = 0;
-                    if (c0 + lane < nn) {
-                        const int4 c1 = col1[c0 + lane];
-                        const float *dtc = dt + lane * kTcM;
-                        stencil_warp(w, dtc, c1, lane, a);
-                    }
-#pragma unroll
-                    for (int c = 0; c < kCls6; ++c) part[(w * 32 + lane) * 33 + c] = a[c];
-                    epi_sync();
-                    // sums of the four quarters: warp w takes columns w, w + 4, ...; lane = class
-                    for (int cl = w; cl < 32; cl += 4) {
-                        const int n = c0 + cl;
-                        if (n < nn && lane < kCls6) {
-                            const int sum = part[cl * 33 + lane] + part[(32 + cl) * 33 + lane] +
-                                            part[(64 + cl) * 33 + lane] +
-                                            part[(96 + cl) * 33 + lane];
-                            const int slot = col[n].z;  // the b side carries -delta
-                            if (sum)
-                                red_add_global(side + (size_t)slot * kMaxClasses + lane,
-                                               (slot & 1) ? -sum : sum);
-                        }
-                    }
-                } else if (qin && fast) {
-                    // per 16 columns: the table lookups first (independent loads), then the
-                    // class-sum updates
-#pragma unroll
-                    for (int h = 0; h < 32; h += 16) {
-                        int cls[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int n = c0 + h + i < nn ? c0 + h + i : nn - 1;
-                            const int2 ci = *reinterpret_cast<const int2 *>(col + n);
-                            const int c = tab2[lt - ci.x];
-                            cls[i] = (c0 + h + i < nn && qpix != ci.y) ? c : -1;
-                        }
+                    int32_t *dtb = dt + (ci & 1u) * (32 * kTcM);
+                    if (have) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (cls[i] >= 0)
-                                atomicAdd(&acc[(c0 + h + i) * 32 + cls[i]],
-                                          __float2int_rn(__uint_as_float(v[h + i])));
+                            dtb[(16 * half + i) * kTcM + row] =
+                                __float2int_rn(__uint_as_float(v[i]));  // an exact integer
                     }
-                } else if (qin) {
+                    epi_sync();
+                    const int n = c0 + lane;
+                    if (n < nn) g6_warp(w, dtb + lane * kTcM, col1[n], lane, side);
+                    ++ci;
+                } else if (have && qin && fast) {
+                    // per column: the table lookup, then the class-sum update
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int n = c0 + i;
+                    for (int i = 0; i < 16; ++i) {
+                        const int n = cc + i;
                         if (n < nn) {
-                            const int4 ci = col[n];
-                            int dx = qx - (ci.w & 0xFFFF), dy = qy - (ci.w >> 16);
+                            const int2 cinfo = *reinterpret_cast<const int2 *>(col + n);
+                            const int c = tab2[lt - cinfo.x];
+                            if (c >= 0 && qpix != cinfo.y)
+                                atomicAdd(reinterpret_cast<int *>(dt) + n * 32 + c,
+                                          __float2int_rn(__uint_as_float(v[i])));
+                        }
+                    }
+                } else if (have && qin) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int n = cc + i;
+                        if (n < nn) {
+                            const int4 cinfo = col[n];
+                            int dx = qx - (cinfo.w & 0xFFFF), dy = qy - (cinfo.w >> 16);
                             dx += dx < -hw ? W : 0;
                             dx -= dx > hw ? W : 0;
                             dy += dy < -hh ? H : 0;
                             dy -= dy > hh ? H : 0;
-                            const int d2 = dx * dx + dy * dy;  // |dx| <= W/2, |dy| <= H/2
-                            if (d2 <= r2) {
-                                const int c = tab[d2];  // -1 for d2 = 0 and empty classes
-                                if (c >= 0 && qpix != ci.y)
-                                    atomicAdd(&acc[n * 32 + c],
+                            const int dd = dx * dx + dy * dy;  // |dx| <= W/2, |dy| <= H/2
+                            if (dd <= r2) {
+                                const int c = tab[dd];  // -1 for dd = 0 and empty classes
+                                if (c >= 0 && qpix != cinfo.y)
+                                    atomicAdd(reinterpret_cast<int *>(dt) + n * 32 + c,
                                               __float2int_rn(__uint_as_float(v[i])));
                             }
                         }
                     }
                 }
             }
-            tc::fence_before_sync();
-            mbar_arrive(&tempty[buf]);
-            epi_sync();
-            // warp w sends the class sums of columns w, w + 4, ...; lane = class
             if (!colpath) {
-                const int lane = et & 31;
-                for (int nb = w; nb < nn; nb += 4 * kFlushBatch) {
+                // warp w sends the class sums of columns w, w + 8, ...; lane = class
+                epi_sync();
+                for (int nb = w; nb < nn; nb += kEpiWarps * kFlushBatch) {
                     int val[kFlushBatch], slot[kFlushBatch];
 #pragma unroll
                     for (int k = 0; k < kFlushBatch; ++k) {
-                        const int n = nb + 4 * k;
+                        const int n = nb + kEpiWarps * k;
                         slot[k] = n < nn ? col[n].z : 0;
-                        val[k] = (n < nn && lane < ncls) ? acc[n * 32 + lane] : 0;
+                        val[k] = (n < nn && lane < ncls) ? dt[n * 32 + lane] : 0;
                         if (slot[k] & 1) val[k] = -val[k];  // the b side carries -delta
                     }
 #pragma unroll
                     for (int k = 0; k < kFlushBatch; ++k)
                         if (val[k]) red_add_global(side + (size_t)slot[k] * kMaxClasses + lane, val[k]);
                 }
+                epi_sync();  // the scratch is free for the next product
             }
-            epi_sync();
             ++jb;
         }
         if (!ok) break;
-        if (et == 0 && d.cnt > 0) pb.tc_cnt[d.pid] = 0;  // cleared for the next pass
+        if (et == 0) pb.tc_cnt[d.pid] = 0;  // cleared for the next pass
     }
 }
 
@@ -663,20 +842,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
     extern __shared__ unsigned char smem_raw[];
     char *smem = reinterpret_cast<char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);
-    uint64_t *full = bars, *empty = bars + kStages;
-    uint64_t *tfull = bars + 2 * kStages, *tempty = tfull + 2, *done = tempty + 2;
+    uint64_t *a_full = bars, *a_empty = a_full + kABoxes;
+    uint64_t *s_full = a_empty + kABoxes, *s_empty = s_full + kASlots;
+    uint64_t *b_full = s_empty + kASlots, *b_empty = b_full + kBStages;
+    uint64_t *acc_full = b_empty + kBStages, *acc_empty = acc_full + 2, *done = acc_empty + 2;
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kOffMisc);
     volatile int *s_abort = reinterpret_cast<volatile int *>(smem + kOffMisc + 4);
     volatile int *s_zero = reinterpret_cast<volatile int *>(smem + kOffMisc + 8);  // stays 0
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
-            mbar_init(&full[i], kProdWarps);
-            mbar_init(&empty[i], 1);
+        for (int i = 0; i < kABoxes; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], kConvWarps);
+        }
+        for (int i = 0; i < kASlots; ++i) {
+            mbar_init(&s_full[i], kConvWarps);
+            mbar_init(&s_empty[i], 1);
+        }
+        for (int i = 0; i < kBStages; ++i) {
+            mbar_init(&b_full[i], kProdWarps);
+            mbar_init(&b_empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], kEpiThreads);
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], kEpiThreads);
         }
         mbar_init(done, 1);
         *s_abort = 0;
@@ -691,12 +880,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
-    if (warp < kEpiWarps)
-        tc_epilogue(args, smem, tfull, tempty, tmem, s_abort);
-    else if (warp < kMmaWarp)
-        tc_produce(args, smem, full, empty, s_abort);
-    else
-        tc_mma(args, smem, full, empty, tfull, tempty, done, tmem, s_abort, s_zero);
+    if (warp < kConvWarp0)
+        tc_epilogue(args, smem, acc_full, acc_empty, tmem, s_abort);
+    else if (warp < kProdWarp0)
+        tc_convert(args, smem, a_full, a_empty, s_full, s_empty, tmem, s_abort);
+    else if (warp < kLoadWarp)
+        tc_produce_b(args, smem, b_full, b_empty, s_abort);
+    else if (warp == kLoadWarp) {
+        if ((threadIdx.x & 31) == 0) tc_load_a(args, smem, a_full, a_empty, s_abort, s_zero);
+    } else
+        tc_mma(args, smem, s_full, s_empty, b_full, b_empty, acc_full, acc_empty, done, tmem,
+               s_abort, s_zero);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -727,8 +921,9 @@ __device__ __forceinline__ void note_patch(int (&idx)[kMaxMet], int (&dist)[kMax
 }
 
 // One warp per couple: the couple's class sums are cleared, its f16 delta row k_b - k_a is
-// written for every stage, and each of its two pixels is appended to the lists of the patches
-// within the radius of it (lanes 0-15: pixel a, 16-31: pixel b, one patch per lane).
+// written for every stage of 64 integrands, and each of its two pixels is appended to the lists
+// of the patches within the radius of it (lanes 0-15: pixel a, 16-31: pixel b, one patch per
+// lane).
 __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
 {
     const Problem &pb = probs[blockIdx.y];
@@ -744,24 +939,47 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
     if (lane < 2 * kMaxClasses / 4)
         reinterpret_cast<int4 *>(pb.side_cls + (size_t)j * 2 * kMaxClasses)[lane] =
             make_int4(0, 0, 0, 0);
-    // deltas, 16 integrands (two f16 pieces of one stage) per lane and step
-    const int nv = (pb.row_bytes >> 6) * 4;
-    for (int v = lane; v < nv; v += 32) {
-        const int e0 = v * 16;  // first integrand
-        const size_t cb = ((size_t)(e0 >> 7) * pb.P) << 7;
-        const uint4 ka = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)a << 7) +
-                                                          (e0 & 127));
-        const uint4 kb = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)b << 7) +
-                                                          (e0 & 127));
-        uint4 o0, o1;
-        bytes_sub_h2(kb.x, ka.x, o0.x, o0.y);
-        bytes_sub_h2(kb.y, ka.y, o0.z, o0.w);
-        bytes_sub_h2(kb.z, ka.z, o1.x, o1.y);
-        bytes_sub_h2(kb.w, ka.w, o1.z, o1.w);
-        uint4 *dst = reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(v >> 2) * pb.M + j) << 6) +
-                                               (v & 3) * 16);
-        dst[0] = o0;
-        dst[1] = o1;
+    const int kst = tc_stages(pb);
+    if (pb.count_bytes == 1) {
+        // 16 integrands (two f16 pieces of one stage) per lane and step
+        const int nv = kst * 4;
+        for (int v = lane; v < nv; v += 32) {
+            const int e0 = v * 16;  // first integrand
+            const size_t cb = ((size_t)(e0 >> 7) * pb.P) << 7;
+            const uint4 ka = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)a << 7) +
+                                                              (e0 & 127));
+            const uint4 kb = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)b << 7) +
+                                                              (e0 & 127));
+            uint4 o0, o1;
+            bytes_sub_h2(kb.x, ka.x, o0.x, o0.y);
+            bytes_sub_h2(kb.y, ka.y, o0.z, o0.w);
+            bytes_sub_h2(kb.z, ka.z, o1.x, o1.y);
+            bytes_sub_h2(kb.w, ka.w, o1.z, o1.w);
+            uint4 *dst = reinterpret_cast<uint4 *>(pb.tc_delta16 +
+                                                   (((size_t)(v >> 2) * pb.M + j) << 6) +
+                                                   (v & 3) * 16);
+            dst[0] = o0;
+            dst[1] = o1;
+        }
+    } else {
+        // 16-bit counts (below 1024): 8 integrands (one f16 piece) per lane and step; a stage
+        // of 64 integrands is one 128-byte chunk
+        const int nv = kst * 8;
+        for (int v = lane; v < nv; v += 32) {
+            const int e0 = v * 8;
+            const size_t cb = ((size_t)(e0 >> 6) * pb.P) << 7;
+            const uint4 ka = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)a << 7) +
+                                                              (e0 & 63) * 2);
+            const uint4 kb = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)b << 7) +
+                                                              (e0 & 63) * 2);
+            uint4 o;
+            o.x = h2_sub(kb.x | kH2Magic, ka.x | kH2Magic);
+            o.y = h2_sub(kb.y | kH2Magic, ka.y | kH2Magic);
+            o.z = h2_sub(kb.z | kH2Magic, ka.z | kH2Magic);
+            o.w = h2_sub(kb.w | kH2Magic, ka.w | kH2Magic);
+            *reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(e0 >> 6) * pb.M + j) << 6) +
+                                       (e0 & 63)) = o;
+        }
     }
     // lanes 0..15 list pixel a, lanes 16..31 pixel b, one patch each, all atomics in parallel
     const int side = lane >> 4, k = lane & 15;
@@ -792,27 +1010,6 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
                 pb.tc_list[(size_t)pid * pb.tc_cap + pos] =
                     make_int4(p, side ? a : b, 2 * j + side, (rx & 0xFFFF) | (ry << 16));
         }
-    }
-}
-
-// f16 copy of the counts: piece v of the copy = 8 integrands of one pixel and stage
-__global__ void k_tc_refresh(const Problem *probs)
-{
-    const Problem &pb = *probs;
-    const long long n = (long long)pb.P * (pb.row_bytes >> 6) * 8;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const long long per = (long long)pb.P * 8;
-        const int ks = (int)(v / per);
-        const int rem = (int)(v - (long long)ks * per);
-        const int p = rem >> 3, pc = rem & 7;
-        const int e0 = ks * 64 + pc * 8;
-        const uint2 k = *reinterpret_cast<const uint2 *>(
-            pb.counts + ((((size_t)(e0 >> 7) * pb.P) + p) << 7) + (e0 & 127));
-        uint4 o;
-        bytes_to_h2(k.x, kBiasCount, o.x, o.y);
-        bytes_to_h2(k.y, kBiasCount, o.z, o.w);
-        *reinterpret_cast<uint4 *>(pb.tc_counts16 + (((size_t)ks * pb.P + p) << 6) + pc * 8) = o;
     }
 }
 
@@ -862,26 +1059,57 @@ __global__ void __launch_bounds__(kListThreads) k_tc_finalize(const Problem *pro
         atomicAdd(&pb.stats[threadIdx.x], (unsigned long long)bstat[threadIdx.x]);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
 }  // namespace
 
 bool tc_supported(const Problem &h)
 {
-    return h.count_bytes == 1 && h.radius >= 1 && h.radius <= 8 && h.W >= 2 * h.radius + 1 &&
+    // counts below 1024 (f16 read as 1024 + k), centred products exact in f32:
+    // T (N / 2) N <= 2^24
+    const bool counts_ok = h.count_bytes == 1 || (h.count_bytes == 2 && h.N <= 512);
+    const bool exact = (long long)h.T * h.N * h.N <= (1ll << 25);
+    return counts_ok && exact && h.radius >= 1 && h.radius <= 8 && h.W >= 2 * h.radius + 1 &&
            h.H >= 2 * h.radius + 1 && h.n_cls <= kMaxClasses && h.row_bytes % 128 == 0;
 }
 
 int tc_units_per_problem(const Problem &h) { return h.tc_npx * h.tc_npy; }
 
-cudaError_t launch_tc_refresh(const Problem *dprob, const std::vector<Problem> &hp,
-                              cudaStream_t st)
+size_t tc_delta_bytes(const Problem &h) { return (size_t)h.M * tc_stages(h) * 64 * 2; }
+
+int tc_tensor_map_bytes() { return kTensorMapBytes; }
+
+// the count planes [chunk][y][x][128 bytes] as a 4-D tensor; one box is a patch (16 x 8 pixels)
+// of one chunk, 128-byte swizzle, zero outside the tile
+cudaError_t encode_tc_tensor_map(const Problem &h, void *out)
 {
-    for (size_t i = 0; i < hp.size(); ++i) {
-        const long long n = (long long)hp[i].P * (hp[i].row_bytes >> 6) * 8;
-        const long long blocks = (n + 255) / 256;
-        k_tc_refresh<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(dprob + i);
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
+    if (!fn) {
+        cudaGetLastError();
+        return cudaErrorNotSupported;
     }
-    note_launches((long long)hp.size());
-    return cudaGetLastError();
+    const cuuint64_t dims[4] = {128u, (cuuint64_t)h.W, (cuuint64_t)h.H,
+                                (cuuint64_t)(h.row_bytes / 128)};
+    const cuuint64_t strides[3] = {128u, (cuuint64_t)h.W * 128u, (cuuint64_t)h.P * 128u};
+    const cuuint32_t box[4] = {128u, (cuuint32_t)kPW, (cuuint32_t)kPH, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const CUresult r =
+        fn(static_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, (void *)h.counts,
+           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t prepare_tc()
@@ -899,7 +1127,7 @@ cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm
     k_tc_lists<<<gw, kListThreads, 0, st>>>(tl.dprob);
     if (all) tm->end(st);
     if (tl.total_units > 0) {
-        const TcArgs a{tl.dprob, tl.n_prob, tl.unit_start, tl.total_units};
+        const TcArgs a{tl.dprob, tl.n_prob, tl.unit_start, tl.total_units, tl.tmaps};
         const int grid = tl.total_units < tl.sms ? tl.total_units : tl.sms;
         if (timed) tm->begin(kKTcStencil, st);
         k_tc_stencil<<<grid, kTcThreads, kSmemBytes, st>>>(a);

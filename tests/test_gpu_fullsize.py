@@ -7,6 +7,7 @@ spawned processes), Eq. 1 and two lockstep passes at 256 x 256; sampled tiles of
 batch in lockstep.  What is checked by properties: after hundreds of passes the count vectors and
 shifts are permutations of the initial ones, Eq. 1 never moved the wrong way, and the fused
 persistent batch equals the plain schedule run alone."""
+import copy
 import os
 
 import numpy as np
@@ -48,12 +49,25 @@ def _sorted_rows(a):
     return a[np.lexsort(a.T[::-1])]
 
 
-def test_multidim_configuration_full_size(pkg):
+@pytest.fixture(scope="module")
+def multidim_refs():
+    """The oracle's two pairs of the 256 x 256 configuration, computed once for the module."""
+    cfg = workloads.c3()[0]
+    W, H, N, T = cfg.width, cfg.height, cfg.n_points, cfg.n_integrands
+    return [oracle.OracleTile(W, H, N, T, seed=0, pair=i, workers=WORKERS) for i in range(2)]
+
+
+@pytest.mark.parametrize("schedule", ["autotuned", "tensor"])
+def test_multidim_configuration_full_size(pkg, multidim_refs, schedule):
     cfg = workloads.c3()[0]
     W, H, N, T = cfg.width, cfg.height, cfg.n_points, cfg.n_integrands
     s = pkg.Sampler(W, H, N, T, seed=0, n_pairs=2)
-    s.autotune(10)
-    refs = [oracle.OracleTile(W, H, N, T, seed=0, pair=i, workers=WORKERS) for i in range(2)]
+    if schedule == "tensor":  # 16-bit counts as centred f16 operands of tcgen05.mma
+        s.set_schedule(pkg.BN_SCHEDULE_TENSOR)
+        assert s.get_schedule()["kind"] == pkg.BN_SCHEDULE_TENSOR
+    else:
+        s.autotune(10)
+    refs = copy.deepcopy(multidim_refs)
     e = s.energy()
     k0 = []
     for i, ref in enumerate(refs):

@@ -54,7 +54,13 @@ LOCKSTEP = [
     (33, 47, 64, 256, 1, 8, 7, 8),      # radius 8: 29 classes, lists up to 768 pixels
     (40, 30, 32, 129, 1, 3, 4, 10),     # radius 3
     (48, 40, 64, 1024, 1, 6, 3, 4),     # T = 1024, 16 stages of 64 integrands
-    (20, 20, 64, 4096, 1, 6, 1, 2),     # largest T: T N^2 = 2^24, the exactness bound
+    (20, 20, 64, 4096, 1, 6, 1, 2),     # largest T of 8-bit counts: T N^2 = 2^24
+    # 16-bit counts (N >= 128), centred f16 operands
+    (32, 32, 256, 64, 1, 6, 3, 10),     # N = 256
+    (45, 37, 128, 200, 2, 6, 4, 8),     # N = 128, two pairs, ragged patches and T
+    (40, 40, 256, 512, 1, 6, 9, 4),     # T N^2 = 2^25: the exactness bound of centred products
+    (33, 29, 512, 100, 1, 3, 2, 6),     # N = 512 (counts up to 512), radius 3
+    (29, 31, 128, 70, 1, 8, 6, 6),      # radius 8 with 16-bit counts
 ]
 
 
@@ -108,7 +114,7 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("cfg", [(128, 128, 64, 1024, 1, 0), (64, 48, 64, 1024, 2, 21),
-                                 (96, 80, 16, 256, 1, 4)])
+                                 (96, 80, 16, 256, 1, 4), (64, 64, 256, 512, 2, 5)])
 def test_tensor_schedule_equals_plain(pkg, cfg):
     """Tiles, logs, energies, counts and statistics bit-identical to the plain schedule."""
     plain = _run(pkg, pkg.BN_SCHEDULE_PLAIN, cfg, 40)
@@ -177,10 +183,11 @@ def test_switching_schedules_mid_run(pkg):
     s.close()
 
 
-@pytest.mark.parametrize("W,H,N,T,r", [(40, 40, 256, 64, 6), (12, 40, 16, 64, 6),
-                                       (40, 6, 16, 64, 3)])
+@pytest.mark.parametrize("W,H,N,T,r", [(40, 40, 256, 1024, 6), (40, 40, 1024, 8, 6),
+                                       (12, 40, 16, 64, 6), (40, 6, 16, 64, 3)])
 def test_tensor_schedule_refused_outside_its_domain(pkg, W, H, N, T, r):
-    """16-bit counts (N > 64) and tiles narrower than 2 radius + 1 are refused."""
+    """Centred products that could leave the exact range of f32 (T N^2 > 2^25), counts of 1024
+    (N = 1024) and tiles narrower than 2 radius + 1 are refused."""
     from paper_2105_12620_gb300 import BnError
     with pytest.raises(BnError):
         pkg.Sampler(W, H, N, T, seed=1, radius=r, schedule=pkg.BN_SCHEDULE_TENSOR)
