@@ -106,7 +106,7 @@ struct SweepPlan {
     bool ready = false;             // built completely; a failed build leaves an empty plan
     bool persistent = false;
     bool tensor = false;            // tensor-core schedule (every problem supports it)
-    int *d_tc_prefix = nullptr;     // [n_prob + 1] prefix sums of 16 x 8 patches
+    int4 *d_tc_units = nullptr;     // [tc_units] (problem, patch, x0, y0) of every 16 x 8 patch
     int tc_units = 0;
     // the problems as the tensor-core kernels see them: the same state plus the plan's per-pass
     // f16 delta rows (allocations in tc_bufs)
@@ -142,8 +142,8 @@ void free_plan(SweepPlan &pl)
     if (pl.d_bar) cudaFree(pl.d_bar);
     if (pl.d_work) cudaFree(pl.d_work);
     if (pl.d_tmaps) cudaFree(pl.d_tmaps);
-    if (pl.d_tc_prefix) cudaFree(pl.d_tc_prefix);
-    pl.d_tc_prefix = nullptr;
+    if (pl.d_tc_units) cudaFree(pl.d_tc_units);
+    pl.d_tc_units = nullptr;
     if (pl.d_tcprob) cudaFree(pl.d_tcprob);
     pl.d_tcprob = nullptr;
     for (void *b : pl.tc_bufs) cudaFree(b);
@@ -409,9 +409,12 @@ int build_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int
                 return fail(BN_ERR_INVALID_ARG, "the tensor-core schedule needs counts below "
                             "1024 (N <= 512), exact centred products (T N^2 <= 2^25), radius "
                             "<= 8 and tile sides of at least 2 radius + 1");
-        std::vector<int> pre((size_t)pl.n_prob + 1, 0);
-        for (int i = 0; i < pl.n_prob; ++i) pre[i + 1] = pre[i] + bn::tc_units_per_problem(hp[i]);
-        pl.tc_units = pre[pl.n_prob];
+        std::vector<int4> units;
+        for (int i = 0; i < pl.n_prob; ++i)
+            for (int pid = 0; pid < bn::tc_units_per_problem(hp[i]); ++pid)
+                units.push_back(make_int4(i, pid, (pid % hp[i].tc_npx) * 16,
+                                          (pid / hp[i].tc_npx) * 8));
+        pl.tc_units = (int)units.size();
         BN_CUDA(bn::prepare_tc());
         pl.tcprob = hp;
         const size_t mb = (size_t)bn::tc_tensor_map_bytes();
@@ -431,8 +434,8 @@ int build_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int
         BN_CUDA(cudaMalloc(&pl.d_tcprob, sizeof(bn::Problem) * pl.tcprob.size()));
         BN_CUDA(cudaMemcpy(pl.d_tcprob, pl.tcprob.data(), sizeof(bn::Problem) * pl.tcprob.size(),
                            cudaMemcpyHostToDevice));
-        BN_CUDA(cudaMalloc(&pl.d_tc_prefix, sizeof(int) * pre.size()));
-        BN_CUDA(cudaMemcpy(pl.d_tc_prefix, pre.data(), sizeof(int) * pre.size(),
+        BN_CUDA(cudaMalloc(&pl.d_tc_units, sizeof(int4) * units.size()));
+        BN_CUDA(cudaMemcpy(pl.d_tc_units, units.data(), sizeof(int4) * units.size(),
                            cudaMemcpyHostToDevice));
         pl.tensor = true;
         pl.first[0] = 0;
@@ -560,7 +563,7 @@ cudaError_t launch_pass(const SweepPlan &pl, const bn::SweepLaunch &sl, cudaStre
                         bn::KernelTimer *tm)
 {
     if (!pl.tensor) return bn::launch_plain_sweep(sl, st, tm);
-    const bn::TcLaunch tl{pl.d_tcprob, sl.n_prob, pl.max_M, pl.d_tc_prefix, pl.tc_units, pl.sms,
+    const bn::TcLaunch tl{pl.d_tcprob, sl.n_prob, pl.max_M, pl.d_tc_units, pl.tc_units, pl.sms,
                           pl.d_tmaps};
     return bn::launch_tc_sweep(tl, st, tm);
 }

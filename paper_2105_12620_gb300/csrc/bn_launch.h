@@ -91,8 +91,8 @@ struct TcLaunch {
     const Problem *dprob;   // device array of problems (each with its tc_delta16 buffer)
     int n_prob;
     int max_M;
-    const int *unit_start;  // device [n_prob + 1] prefix sums of 16 x 8 patches
-    int total_units;
+    const int4 *units;      // device [total_units] (problem, patch, x0, y0) of every 16 x 8
+    int total_units;        //   patch, problem by problem
     int sms;
     const char *tmaps;      // device [n_prob] tensor maps of the count planes
 };

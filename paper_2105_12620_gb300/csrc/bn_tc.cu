@@ -21,19 +21,23 @@
 //   k_tc_lists     one warp per couple: its class sums cleared, its f16 delta row k_b - k_a
 //                  written per stage of 64 integrands, each of its pixels appended to the list
 //                  of every patch within the radius
-//   k_tc_stencil   one CTA of 16 warps per SM over the patches:
+//   k_tc_stencil   one CTA of 24 warps per SM over the patches:
 //                    A loader (1 thread)  one TMA box per 128-byte count chunk: the patch's 128
 //                                         pixels x 128 bytes (zero outside the tile), 128-byte
 //                                         swizzle, into a ring of four boxes
-//                    4 converter warps    thread = patch pixel = tensor-memory lane: its chunk
-//                                         -> exact centred f16 -> tensor memory (tcgen05.st),
-//                                         64 integrands per slot, four slots
-//                    2 producer warps     cp.async of the listed couples' delta rows (B)
-//                                         straight into the 128-byte swizzled K-major layout,
-//                                         five stages of 64 integrands
-//                    1 MMA warp           four tcgen05.mma (A from tensor memory, B from shared
-//                                         memory, K = 16) per stage into one of two
-//                                         accumulators (M = 128, N <= 160)
+//                    8 converter warps    thread = patch pixel = tensor-memory lane (two warps
+//                                         per lane quadrant, one half of the integrands each):
+//                                         its chunk -> exact centred f16 -> tensor memory
+//                                         (tcgen05.st), 64 integrands per slot
+//                    4 producer warps     cp.async of the listed couples' delta rows (B)
+//                                         straight into the 128-byte swizzled K-major layout;
+//                                         a ring of six stages of 64 integrands, each an A slot
+//                                         and a delta tile, full when the converters and every
+//                                         producer thread's copies have arrived
+//                    3 MMA warps          stage g issued by warp g mod 3: four tcgen05.mma (A
+//                                         from tensor memory, B from shared memory, K = 16)
+//                                         into one of two accumulators (M = 128, N <= 160),
+//                                         which the epilogue zeroes as it reads them
 //                    8 epilogue warps     16 accumulator columns per warp and step, transposed
 //                                         through shared memory 32 columns at a time; for
 //                                         radius 6 each warp owns whole distance classes and
@@ -58,19 +62,21 @@ namespace {
 
 constexpr int kPW = 16, kPH = 8, kTcM = kPW * kPH;  // patch: M = 128 pixels
 constexpr int kNB = 160;                             // listed pixels per product (N)
-constexpr int kABoxes = 4;                           // ring of count boxes (TMA)
-constexpr int kASlots = 4;                           // A slots of 64 integrands in tensor memory
-constexpr int kBStages = 5;                          // ring of delta stages of 64 integrands
-constexpr int kBLook = 3;                            // delta stages in flight per thread
+constexpr int kABoxes = 3;                           // ring of count boxes (TMA)
+constexpr int kStages = 6;                           // ring of stages of 64 integrands: an A slot in
+                                                     // tensor memory and a delta tile in shared
+                                                     // memory each, one full and one empty barrier
 constexpr int kBoxBytes = kTcM * 128;                // 16 KB: 128 pixels x 128 count bytes
 constexpr int kBStageBytes = kNB * 128;              // 20 KB: 160 rows x 64 f16
-constexpr int kEpiWarps = 8, kConvWarps = 4, kProdWarps = 2;
+constexpr int kEpiWarps = 8, kConvWarps = 8, kProdWarps = 4;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kConvWarp0 = kEpiWarps;                // converter warp c reads lane quadrant c
+constexpr int kConvWarp0 = kEpiWarps;                // converter warp c: lane quadrant c mod 4,
+                                                     // integrand half c / 4 of every slot
 constexpr int kProdWarp0 = kConvWarp0 + kConvWarps;
 constexpr int kLoadWarp = kProdWarp0 + kProdWarps;
-constexpr int kMmaWarp = kLoadWarp + 1;
-constexpr int kTcThreads = (kMmaWarp + 1) * 32;      // 512
+constexpr int kMmaWarp0 = kLoadWarp + 1;
+constexpr int kMmaWarps = 3;                         // stage g is issued by MMA warp g mod 3
+constexpr int kTcThreads = (kMmaWarp0 + kMmaWarps) * 32;  // 608
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kBTasks = kNB * 8 / kProdThreads;      // 16-byte pieces per producer thread
 constexpr uint32_t kTmemCols = 512, kAccCols = kNB;  // accumulators at columns 0 and 160
@@ -80,33 +86,44 @@ constexpr long long kSpin = 1ll << 31;               // ~1 s at 2 GHz
 constexpr unsigned long long kErrTc = 3ull;
 constexpr int kFlushBatch = 5;                       // class-sum rows sent per batch
 constexpr int kTensorMapBytes = 128;                 // one CUtensorMap per problem
+constexpr int kUnitTab = 64;                         // patches of one CTA per launch (a pass with
+                                                     // more is split over launches)
 static_assert(kConvWarp0 % 4 == 0, "lane quadrants of the converter warps");
-static_assert(kColA + 32 * kASlots <= kTmemCols, "tensor memory");
-static_assert(kBTasks * kProdThreads == 8 * kNB && kProdThreads == 64, "producer rows");
+static_assert(kColA + 32 * kStages <= kTmemCols, "tensor memory");
+constexpr int kProdRowStep = kProdThreads / 8;       // rows between a producer thread's tasks
+static_assert(kBTasks * kProdThreads == 8 * kNB && kProdRowStep % 8 == 0, "producer rows");
 
 // shared memory layout (offsets from a 1024-byte aligned base)
 constexpr int kOffA = 0;                                    // count boxes, swizzled
 constexpr int kOffB = kOffA + kABoxes * kBoxBytes;          // delta stages, swizzled
-constexpr int kOffDt = kOffB + kBStages * kBStageBytes;     // epilogue scratch: int32 [2][32][128]
-constexpr int kDtBytes = 2 * 32 * kTcM * 4;                 //   transposes, or int32 [kNB][32]
-constexpr int kOffCol = kOffDt + kDtBytes;                  //   class sums of the table paths
+constexpr int kOffDt = kOffB + kStages * kBStageBytes;      // epilogue: int32 [32][128] transpose
+constexpr int kDtBytes = 32 * kTcM * 4;
+constexpr int kAccStride = 19;                              // class sums of one listed pixel
+constexpr int kOffAcc6 = kOffDt + kDtBytes;                 // int32 [kNB][kAccStride]: class sums
+constexpr int kAcc6Bytes = kNB * kAccStride * 4;            //   of a product's pixels (radius 6)
+// the table paths' class sums, int32 [kNB][32], overlay the transpose and kOffAcc6 (a product
+// uses one path; products are separated by epilogue barriers)
+constexpr int kOffCol = kOffAcc6 + kAcc6Bytes;              // int4 [2][kNB] x 2: listed pixels
 constexpr int kOffTab = kOffCol + 2 * 2 * kNB * 16;         // int32 [80] class of a squared distance
 constexpr int kOffTab2 = kOffTab + 80 * 4;                  // int8 [2-D offset] class (table path)
 constexpr int kTab2Max = 1664;                              // (2 (16 + 8) + 1) x (2 (8 + 8) + 1)
-constexpr int kOffBar = kOffTab2 + kTab2Max;                // mbarriers
-constexpr int kNBars = 2 * kABoxes + 2 * kASlots + 2 * kBStages + 4 + 1;
+constexpr int kOffUnits = kOffTab2 + kTab2Max;              // TcUnit [kUnitTab]: this CTA's patches
+constexpr int kOffBar = kOffUnits + kUnitTab * 64;          // mbarriers
+constexpr int kNBars = 2 * kABoxes + 2 * kStages + 4 + kMmaWarps;
 constexpr int kOffMisc = kOffBar + kNBars * 8;              // tensor-memory base, abort flags
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;
-static_assert(kNB * 32 * 4 <= kDtBytes, "class sums of the table paths");
+static_assert(kNB * 32 * 4 <= kDtBytes + kAcc6Bytes, "class sums of the table paths");
 static_assert(kOffB % 1024 == 0 && kBStageBytes % 1024 == 0 && kOffDt % 16 == 0, "alignment");
-static_assert(kOffBar % 8 == 0, "mbarrier alignment");
+static_assert(kOffUnits % 16 == 0 && kOffBar % 8 == 0, "table and mbarrier alignment");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 struct TcArgs {
     const Problem *probs;
     int n_prob;
-    const int *unit_start;  // [n_prob + 1] prefix sums of patches
-    int total_units;
+    const int4 *units;      // [all patches] (problem, patch, x0, y0)
+    int unit_begin;         // this launch's patches: unit_begin .. unit_begin + unit_count - 1,
+    int unit_count;         //   CTA c taking the contiguous run from unit_begin + c * per
+    int per;
     const char *tmaps;      // [n_prob] tensor maps of the count planes (kTensorMapBytes each)
 };
 
@@ -126,15 +143,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  "r"(bytes)
                  : "memory");
 }
+// test for the completion of the phase of the given parity; the thread may be suspended in
+// hardware (no instructions issued) for up to kSuspendNs while the phase is incomplete
+constexpr uint32_t kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(tc::saddr(bar)), "r"(parity)
+        : "r"(tc::saddr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -165,29 +185,45 @@ __device__ __forceinline__ void red_add_global(int32_t *p, int v)
     // no compiler memory barrier: nothing in the kernel reads these sums
     asm volatile("red.global.add.s32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v));
 }
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint64_t policy)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
-                 "l"(__cvta_generic_to_global(src))
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst),
+                 "l"(__cvta_generic_to_global(src)), "l"(policy)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit()
+// one arrival on *bar once every cp.async this thread issued before has completed (the
+// barrier's count includes this arrival: no pending-count increment)
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar)
 {
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::saddr(bar))
+                 : "memory");
 }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
+__device__ __forceinline__ void cp_async_wait_all()
 {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+// L2 cache policies: data read once (the count boxes) is evicted first, so that the delta rows,
+// which several patches read, stay in L2
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 // 4-D tiled TMA load into shared memory, completion counted in bytes on *bar
 __device__ __forceinline__ void tma_load_4d(void *dst, const char *tmap, int c0, int c1, int c2,
-                                            int c3, uint64_t *bar)
+                                            int c3, uint64_t *bar, uint64_t policy)
 {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(tc::saddr(dst)),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::saddr(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(tc::saddr(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::saddr(bar)), "l"(policy)
         : "memory");
 }
 // named barrier of the epilogue warps
@@ -206,19 +242,6 @@ __device__ __forceinline__ bool epi_any(bool v)
         : "r"((uint32_t)v), "n"(kEpiThreads)
         : "memory");
     return r != 0;
-}
-
-__device__ __forceinline__ int find_problem(const int *start, int n, int u)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(start + mid) <= u)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
 }
 
 // f16x2 of an unsigned 16-bit pair below 1024: each half read as 1024 + value (exact)
@@ -249,29 +272,45 @@ __host__ __device__ __forceinline__ int tc_stages(const Problem &pb)
     return pb.row_bytes / (64 * pb.count_bytes);
 }
 
-// The unit decode shared by the roles: the same global sequence of patches and of products on
-// every role, from values that do not change during the launch.
+// The CTA's patches in order, with the fields of their problems the roles need, decoded once
+// per launch into shared memory by all threads at the start: every role walks the same sequence
+// of patches and products without a global-memory load on the way.
+struct TcUnit {
+    int pi, pid, cnt, xy;    // problem, patch, listed pixels of this pass, x0 | y0 << 16
+    int wh, geom, nr, M;     // W | H << 16; row_bytes | count_bytes << 16;
+                             // N | radius << 16 | classes << 24; couples per pass
+    const int4 *list;        // the patch's list of proposed pixels
+    const uint16_t *delta;   // the problem's per-pass delta rows
+    int32_t *side;           // the problem's class sums
+    int flags;               // kUnitTable: 2-D table path holds; kUnitStatic6: radius-6 path
+    int pad;
+};
+static_assert(sizeof(TcUnit) == 64, "unit table entry");
+constexpr int kUnitTable = 1, kUnitStatic6 = 2;
 struct Unit {
-    const Problem *pb;
+    const TcUnit *t;
     int pid, cnt, x0, y0;
 };
-__device__ __forceinline__ Unit decode_unit(const TcArgs &args, int u, int &pi)
+__device__ __forceinline__ Unit unit_at(const TcUnit *utab, int k, int &pi)
 {
-    pi = find_problem(args.unit_start, args.n_prob, u);
+    const TcUnit *t = utab + k;
+    pi = t->pi;
     Unit d;
-    d.pb = args.probs + pi;
-    const Problem &pb = *d.pb;
-    d.pid = u - __ldg(args.unit_start + pi);
-    const long long s = pb.ctr[0];
-    int c = 0;
-    if (s < pb.ctr[1]) {
-        c = pb.tc_cnt[d.pid];
-        c = c < pb.tc_cap ? c : pb.tc_cap;
-    }
-    d.cnt = c;
-    d.x0 = (d.pid % pb.tc_npx) * kPW;
-    d.y0 = (d.pid / pb.tc_npx) * kPH;
+    d.t = t;
+    d.pid = t->pid;
+    d.cnt = t->cnt;
+    d.x0 = t->xy & 0xFFFF;
+    d.y0 = t->xy >> 16;
     return d;
+}
+__device__ __forceinline__ int unit_w(const Unit &d) { return d.t->wh & 0xFFFF; }
+__device__ __forceinline__ int unit_h(const Unit &d) { return d.t->wh >> 16; }
+__device__ __forceinline__ int unit_row_bytes(const Unit &d) { return d.t->geom & 0xFFFF; }
+__device__ __forceinline__ int unit_count_bytes(const Unit &d) { return d.t->geom >> 16; }
+// stages of 64 integrands of the patch's count rows
+__device__ __forceinline__ int unit_stages(const Unit &d)
+{
+    return unit_row_bytes(d) / (64 * unit_count_bytes(d));
 }
 
 // 2-D class table of the epilogue's table path: offsets (dx, dy) from a proposed pixel to a
@@ -383,41 +422,65 @@ __device__ __forceinline__ void g6_add(const int32_t *dtc, int plx, int ply, int
         a[k] += in ? x : 0;
     }
 }
-// warp E's class K of the listed pixel sent to the couple's class sums (the b side carries
-// -delta)
+// warp E's class K of the listed pixel, stored in the pixel's row of class sums (each class of
+// each listed pixel has one writer: the owning warp's lane)
 template <int E, int K>
-__device__ __forceinline__ void g6_send(const int (&a)[kGrpMaxCls], int32_t *side, int slot)
+__device__ __forceinline__ void g6_store(const int (&a)[kGrpMaxCls], int32_t *accrow)
 {
     if constexpr (K < kG6.ncls[E]) {
         constexpr int c = kG6.cls[E][K];
-        if (a[K]) red_add_global(side + (size_t)slot * kMaxClasses + c, (slot & 1) ? -a[K] : a[K]);
+        accrow[c] = a[K];
     }
 }
 template <int E, int... I>
-__device__ __forceinline__ void g6_sum(const int32_t *dtc, int4 c1, int lane, int32_t *side,
+__device__ __forceinline__ void g6_sum(const int32_t *dtc, int4 c1, int lane, int32_t *accrow,
                                        std::integer_sequence<int, I...>)
 {
     int a[kGrpMaxCls] = {0, 0, 0, 0};
     (g6_add<E, I>(dtc, c1.x, c1.y, c1.z, lane, a), ...);
-    g6_send<E, 0>(a, side, c1.w);
-    g6_send<E, 1>(a, side, c1.w);
-    g6_send<E, 2>(a, side, c1.w);
-    g6_send<E, 3>(a, side, c1.w);
+    g6_store<E, 0>(a, accrow);
+    g6_store<E, 1>(a, accrow);
+    g6_store<E, 2>(a, accrow);
+    g6_store<E, 3>(a, accrow);
 }
 // warp w's classes for the listed pixel of this lane
 __device__ __forceinline__ void g6_warp(int w, const int32_t *dtc, int4 c1, int lane,
-                                        int32_t *side)
+                                        int32_t *accrow)
 {
     using Seq = std::make_integer_sequence<int, kGrpMaxOff>;
     switch (w) {
-    case 0: g6_sum<0>(dtc, c1, lane, side, Seq{}); break;
-    case 1: g6_sum<1>(dtc, c1, lane, side, Seq{}); break;
-    case 2: g6_sum<2>(dtc, c1, lane, side, Seq{}); break;
-    case 3: g6_sum<3>(dtc, c1, lane, side, Seq{}); break;
-    case 4: g6_sum<4>(dtc, c1, lane, side, Seq{}); break;
-    case 5: g6_sum<5>(dtc, c1, lane, side, Seq{}); break;
-    case 6: g6_sum<6>(dtc, c1, lane, side, Seq{}); break;
-    default: g6_sum<7>(dtc, c1, lane, side, Seq{}); break;
+    case 0: g6_sum<0>(dtc, c1, lane, accrow, Seq{}); break;
+    case 1: g6_sum<1>(dtc, c1, lane, accrow, Seq{}); break;
+    case 2: g6_sum<2>(dtc, c1, lane, accrow, Seq{}); break;
+    case 3: g6_sum<3>(dtc, c1, lane, accrow, Seq{}); break;
+    case 4: g6_sum<4>(dtc, c1, lane, accrow, Seq{}); break;
+    case 5: g6_sum<5>(dtc, c1, lane, accrow, Seq{}); break;
+    case 6: g6_sum<6>(dtc, c1, lane, accrow, Seq{}); break;
+    default: g6_sum<7>(dtc, c1, lane, accrow, Seq{}); break;
+    }
+}
+// a product's class sums sent to the couples' class sums in global memory: warp w takes the
+// listed pixels w, w + 8, ..., lane = class, so each reduction covers one pixel's 18
+// contiguous sums (the b side carries -delta); the loads of a batch are issued before its
+// reductions
+__device__ __forceinline__ void g6_flush(const int32_t *acc, const int4 *col1, int nn, int w,
+                                         int lane, int32_t *side)
+{
+    constexpr int kB = 4;
+    for (int n0 = w; n0 < nn; n0 += kEpiWarps * kB) {
+        int v[kB], slot[kB];
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+            const int n = n0 + kEpiWarps * t;
+            const bool on = n < nn && lane < kCls6;
+            v[t] = on ? acc[n * kAccStride + lane] : 0;
+            slot[t] = on ? col1[n].w : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < kB; ++t)
+            if (v[t])
+                red_add_global(side + (size_t)slot[t] * kMaxClasses + lane,
+                               (slot[t] & 1) ? -v[t] : v[t]);
     }
 }
 
@@ -435,16 +498,18 @@ __device__ __forceinline__ bool classes_match6(const int32_t *d2, std::integer_s
 // ---- A loader (one thread) -------------------------------------------------------------------
 // For every product, one TMA box per 128-byte count chunk: the patch's 16 x 8 pixels x 128
 // bytes (8-bit counts: 128 integrands; 16-bit: 64), zero outside the tile.
-__device__ void tc_load_a(const TcArgs &args, char *smem, uint64_t *a_full, uint64_t *a_empty,
-                          volatile int *abort_flag, volatile int *no_abort)
+__device__ void tc_load_a(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
+                          uint64_t *a_full, uint64_t *a_empty, volatile int *abort_flag,
+                          volatile int *no_abort)
 {
     uint32_t g = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+    const uint64_t pol = policy_evict_first();
+    for (int ku = 0; ku < nu && ok; ++ku) {
         int pi;
-        const Unit d = decode_unit(args, u, pi);
+        const Unit d = unit_at(utab, ku, pi);
         if (d.cnt <= 0) continue;
-        const int nbox = d.pb->row_bytes >> 7;
+        const int nbox = unit_row_bytes(d) >> 7;
         const char *tmap = args.tmaps + (size_t)pi * kTensorMapBytes;
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB)
             for (int c = 0; c < nbox; ++c) {
@@ -455,7 +520,7 @@ __device__ void tc_load_a(const TcArgs &args, char *smem, uint64_t *a_full, uint
                 }
                 mbar_arrive_expect_tx(&a_full[slot], kBoxBytes);
                 tma_load_4d(smem + kOffA + slot * kBoxBytes, tmap, 0, d.x0, d.y0, c,
-                            &a_full[slot]);
+                            &a_full[slot], pol);
                 ++g;
             }
     }
@@ -468,28 +533,30 @@ __device__ void tc_load_a(const TcArgs &args, char *smem, uint64_t *a_full, uint
 }
 
 // ---- converter warps ---------------------------------------------------------------------------
-// Thread = patch pixel = tensor-memory lane (warp c of the group owns lane quadrant c): reads its
-// row of the box (128 bytes), converts it to centred f16 and stores 64 integrands per slot.
-__device__ void tc_convert(const TcArgs &args, char *smem, uint64_t *a_full, uint64_t *a_empty,
-                           uint64_t *s_full, uint64_t *s_empty, uint32_t tmem,
-                           volatile int *abort_flag)
+// Thread = patch pixel = tensor-memory lane (warp c of the group owns lane quadrant c mod 4 and
+// integrands 32 (c / 4) .. 32 (c / 4) + 31 of every slot): reads its part of its row of the box,
+// converts it to centred f16 and stores 16 columns of the slot.
+__device__ void tc_convert(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
+                           uint64_t *a_full, uint64_t *a_empty, uint64_t *full,
+                           uint64_t *empty, uint32_t tmem, volatile int *abort_flag)
 {
-    const int ct = threadIdx.x - kConvWarp0 * 32;  // 0 .. 127
-    const int lane = ct & 31;
+    const int cw = (threadIdx.x >> 5) - kConvWarp0;  // 0 .. kConvWarps - 1
+    const int lane = threadIdx.x & 31;
+    const int ct = 32 * (cw & 3) + lane;             // patch pixel, tensor-memory lane
+    const int half = cw >> 2;
     const int lx = ct & 15, ly = ct >> 4;
     const uint32_t lane_base = (uint32_t)(ct & ~31) << 16;
     uint32_t gb = 0, gs = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+    for (int ku = 0; ku < nu && ok; ++ku) {
         int pi;
-        const Unit d = decode_unit(args, u, pi);
+        const Unit d = unit_at(utab, ku, pi);
         if (d.cnt <= 0) continue;
-        const Problem &pb = *d.pb;
-        const bool qin = d.x0 + lx < pb.W && d.y0 + ly < pb.H;
-        const int nbox = pb.row_bytes >> 7;
-        const bool wide = pb.count_bytes == 2;
+        const bool qin = d.x0 + lx < unit_w(d) && d.y0 + ly < unit_h(d);
+        const int nbox = unit_row_bytes(d) >> 7;
+        const bool wide = unit_count_bytes(d) == 2;
         // 1024 + k - (1024 + N/2) = k - N/2, exact
-        const uint32_t hb = 0x6400u + (uint32_t)(pb.N >> 1);
+        const uint32_t hb = 0x6400u + (uint32_t)((d.t->nr & 0xFFFF) >> 1);
         const uint32_t bias = hb | (hb << 16);
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB)
             for (int c = 0; c < nbox; ++c) {
@@ -499,31 +566,30 @@ __device__ void tc_convert(const TcArgs &args, char *smem, uint64_t *a_full, uin
                     break;
                 }
                 const char *row = smem + kOffA + slot * kBoxBytes + ct * 128;
-                uint4 w[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    w[j] = *reinterpret_cast<const uint4 *>(row + ((j ^ (ct & 7)) << 4));
                 const int nsub = wide ? 1 : 2;
                 for (int sb = 0; sb < nsub; ++sb) {
-                    const uint32_t as = gs % kASlots, ause = gs / kASlots;
-                    if (!tc_wait_warp(&s_empty[as], (ause & 1u) ^ 1u, abort_flag)) {
+                    const uint32_t as = gs % kStages, ause = gs / kStages;
+                    if (!tc_wait_warp(&empty[as], (ause & 1u) ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    uint32_t o[32];
-                    if (wide) {  // 64 integrands of 16 bits: one f16x2 per word
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            o[4 * j + 0] = h2_sub(w[j].x | kH2Magic, bias);
-                            o[4 * j + 1] = h2_sub(w[j].y | kH2Magic, bias);
-                            o[4 * j + 2] = h2_sub(w[j].z | kH2Magic, bias);
-                            o[4 * j + 3] = h2_sub(w[j].w | kH2Magic, bias);
-                        }
-                    } else {  // bytes 64 sb .. 64 sb + 63: two f16x2 per word
+                    uint32_t o[16];
+                    if (wide) {  // integrands 32 half .. of 64 of 16 bits: one f16x2 per word
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const uint4 x = sb ? w[4 + j] : w[j];
+                            const uint4 x = *reinterpret_cast<const uint4 *>(
+                                row + (((4 * half + j) ^ (ct & 7)) << 4));
+                            o[4 * j + 0] = h2_sub(x.x | kH2Magic, bias);
+                            o[4 * j + 1] = h2_sub(x.y | kH2Magic, bias);
+                            o[4 * j + 2] = h2_sub(x.z | kH2Magic, bias);
+                            o[4 * j + 3] = h2_sub(x.w | kH2Magic, bias);
+                        }
+                    } else {  // bytes 64 sb + 32 half .. + 31: two f16x2 per word
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const uint4 x = *reinterpret_cast<const uint4 *>(
+                                row + (((4 * sb + 2 * half + j) ^ (ct & 7)) << 4));
                             bytes_to_h2(x.x, bias, o[8 * j + 0], o[8 * j + 1]);
                             bytes_to_h2(x.y, bias, o[8 * j + 2], o[8 * j + 3]);
                             bytes_to_h2(x.z, bias, o[8 * j + 4], o[8 * j + 5]);
@@ -532,12 +598,12 @@ __device__ void tc_convert(const TcArgs &args, char *smem, uint64_t *a_full, uin
                     }
                     if (!qin) {  // pixels outside a ragged tile: zero rows
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) o[i] = 0u;
+                        for (int i = 0; i < 16; ++i) o[i] = 0u;
                     }
-                    tc::tmem_st32(tmem + lane_base + kColA + 32u * as, o);
+                    tc::tmem_st16(tmem + lane_base + kColA + 32u * as + 16u * half, o);
                     tc::fence_before_sync();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&s_full[as]);
+                    if (lane == 0) mbar_arrive(&full[as]);
                     ++gs;
                 }
                 __syncwarp();
@@ -551,161 +617,199 @@ __device__ void tc_convert(const TcArgs &args, char *smem, uint64_t *a_full, uin
 // ---- producer warps (B) ------------------------------------------------------------------------
 // A stage holds up to kNB delta rows of 64 integrands, each row eight 16-byte pieces, copied by
 // cp.async straight into the swizzled slots (piece j of row r in slot j ^ (r mod 8)).  Producer
-// thread pt owns piece pt mod 8 of rows pt / 8 + 8 k: a warp copies four whole rows per
-// instruction.
-__device__ __forceinline__ void publish_b(uint64_t *b_full, uint32_t gi)
+// thread pt owns piece pt mod 8 of rows pt / 8 + kProdRowStep k: a warp copies four whole rows
+// per instruction.  Each thread's copies of a stage arrive on the stage's barrier when they land
+// (the barrier counts every producer thread), so up to kStages stages are in flight.  A warp
+// issues cp.async at about 10 bytes per clock, so four warps share the stage.
+// the first (first = true) or the next product of this CTA: its patch (table index) and first
+// listed entry; false past the last one
+__device__ __forceinline__ bool next_product(const TcArgs &args, const TcUnit *utab, int nu, int &ku,
+                                             int &n0, Unit &d, int &pi, bool first)
 {
-    tc::fence_async_smem();
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&b_full[gi % kBStages]);
-}
-
-__device__ void tc_produce_b(const TcArgs &args, char *smem, uint64_t *b_full, uint64_t *b_empty,
-                             volatile int *abort_flag)
-{
-    const int pt = threadIdx.x - kProdWarp0 * 32;  // 0 .. 63
-    const int piece = pt & 7, r0 = pt >> 3;          // rows r0 + 8 k: r mod 8 = r0, r / 8 = k
-    const uint32_t dpos = tc::saddr(smem + kOffB) + (uint32_t)(r0 * 128 + ((piece ^ r0) << 4));
-    uint32_t g = 0;
-    bool ok = true;
-    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
-        int pi;
-        const Unit d = decode_unit(args, u, pi);
-        if (d.cnt <= 0) continue;
-        const Problem &pb = *d.pb;
-        const int kst = tc_stages(pb);
-        const uint16_t *const del = pb.tc_delta16 + 8 * piece;
-        const size_t dplane = (size_t)pb.M << 6;  // f16 per stage
-        const int4 *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
-        for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
-            const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
-            int idx[kBTasks];  // couple of each task's row (rows nn .. kNB - 1 stay unloaded:
-                               // they feed columns the epilogue ignores)
-#pragma unroll
-            for (int k = 0; k < kBTasks; ++k) {
-                const int row = r0 + 8 * k;
-                idx[k] = row < nn ? (list[n0 + row].z >> 1) : -1;
-            }
-            for (int ks = 0; ks < kst; ++ks) {
-                const uint32_t slot = g % kBStages, use = g / kBStages;
-                if (!tc_wait_warp(&b_empty[slot], (use & 1u) ^ 1u, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t st = dpos + slot * kBStageBytes;
-                const uint16_t *cd = del + (size_t)ks * dplane;
-#pragma unroll
-                for (int k = 0; k < kBTasks; ++k)
-                    if (idx[k] >= 0) cp_async16(st + k * 1024, cd + ((size_t)idx[k] << 6));
-                cp_async_commit();
-                if (g >= (uint32_t)kBLook) {
-                    cp_async_wait<kBLook>();
-                    publish_b(b_full, g - kBLook);
-                }
-                ++g;
-            }
+    if (!first && n0 + kNB < d.cnt) {
+        n0 += kNB;
+        return true;
+    }
+    if (!first) ++ku;
+    for (; ku < nu; ++ku) {
+        d = unit_at(utab, ku, pi);
+        if (d.cnt > 0) {
+            n0 = 0;
+            return true;
         }
     }
-    cp_async_wait<0>();
-    if (ok) {  // the last kBLook stages, oldest first
-        for (uint32_t b = kBLook; b >= 1; --b)
-            if (g >= b) publish_b(b_full, g - b);
+    return false;
+}
+
+// couple of each of this thread's rows of a product (-1: rows nn .. kNB - 1 stay unloaded, they
+// feed columns the epilogue ignores)
+__device__ __forceinline__ void product_rows(const Unit &d, int n0, int r0, int (&idx)[kBTasks])
+{
+    const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
+    const int4 *list = d.t->list + n0;
+#pragma unroll
+    for (int k = 0; k < kBTasks; ++k) {
+        const int row = r0 + kProdRowStep * k;
+        idx[k] = row < nn ? (list[row].z >> 1) : -1;
     }
 }
 
-// ---- MMA warp ----------------------------------------------------------------------------------
-__device__ void tc_mma(const TcArgs &args, char *smem, uint64_t *s_full, uint64_t *s_empty,
-                       uint64_t *b_full, uint64_t *b_empty, uint64_t *acc_full,
-                       uint64_t *acc_empty, uint64_t *done, uint32_t tmem,
-                       volatile int *abort_flag, volatile int *no_abort)
+__device__ void tc_produce_b(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
+                             uint64_t *full, uint64_t *empty, volatile int *abort_flag)
+{
+    const int pt = threadIdx.x - kProdWarp0 * 32;
+    // rows r0 + kProdRowStep k: r mod 8 = r0 mod 8, r / 8 = r0 / 8 + (kProdRowStep / 8) k
+    const int piece = pt & 7, r0 = pt >> 3;
+    const uint32_t dpos = tc::saddr(smem + kOffB) +
+                          (uint32_t)((r0 >> 3) * 1024 + (r0 & 7) * 128 + ((piece ^ (r0 & 7)) << 4));
+    uint32_t g = 0;
+    bool ok = true;
+    const uint64_t pol = policy_evict_last();
+    int ku = 0, n0 = 0, pi = 0;
+    Unit d{};
+    bool have = next_product(args, utab, nu, ku, n0, d, pi, true);
+    int idx[kBTasks];
+    if (have) product_rows(d, n0, r0, idx);
+    while (have && ok) {
+        // the next product's rows are read while this one's stages are copied
+        int ku2 = ku, n02 = n0, pi2 = pi;
+        Unit d2 = d;
+        const bool have2 = next_product(args, utab, nu, ku2, n02, d2, pi2, false);
+        int idx2[kBTasks];
+        if (have2) product_rows(d2, n02, r0, idx2);
+        const int kst = unit_stages(d);
+        const uint16_t *const del = d.t->delta + 8 * piece;
+        const size_t dplane = (size_t)d.t->M << 6;  // f16 per stage
+        for (int ks = 0; ks < kst; ++ks) {
+            const uint32_t slot = g % kStages, use = g / kStages;
+            if (!tc_wait_warp(&empty[slot], (use & 1u) ^ 1u, abort_flag)) {
+                ok = false;
+                break;
+            }
+            const uint32_t st = dpos + slot * kBStageBytes;
+            const uint16_t *cd = del + (size_t)ks * dplane;
+#pragma unroll
+            for (int k = 0; k < kBTasks; ++k)
+                if (idx[k] >= 0)
+                    cp_async16(st + k * (kProdRowStep / 8) * 1024, cd + ((size_t)idx[k] << 6), pol);
+            cp_async_arrive(&full[slot]);
+            ++g;
+        }
+        ku = ku2;
+        n0 = n02;
+        pi = pi2;
+        d = d2;
+        have = have2;
+#pragma unroll
+        for (int k = 0; k < kBTasks; ++k) idx[k] = idx2[k];
+    }
+    cp_async_wait_all();  // nothing in flight when the CTA leaves
+}
+
+// ---- MMA warps ------------------------------------------------------------------------------
+// Stage g of the CTA's sequence is issued by MMA warp g mod kMmaWarps, so that while one warp
+// waits for its operands and commits its releases the others keep the tensor core's short
+// issue queue filled.  The products are exact integers in f32 (no rounding), so the order in
+// which the warps' products accumulate does not matter; every product accumulates onto an
+// accumulator the epilogue has zeroed.  A product is complete when every MMA warp has committed
+// it (acc_full counts kMmaWarps arrivals).
+__device__ void tc_mma(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
+                       uint64_t *full, uint64_t *empty, uint64_t *acc_full, uint64_t *acc_empty,
+                       uint64_t *done, uint32_t tmem, volatile int *abort_flag,
+                       volatile int *no_abort)
 {
     const int lane = threadIdx.x & 31;
+    const int mw = (threadIdx.x >> 5) - kMmaWarp0;  // 0 .. kMmaWarps - 1
     const uint32_t sbase = tc::saddr(smem + kOffB);
     uint32_t g = 0, jb = 0;
     bool ok = true, issued = false;
-    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+    for (int ku = 0; ku < nu && ok; ++ku) {
         int pi;
-        const Unit d = decode_unit(args, u, pi);
+        const Unit d = unit_at(utab, ku, pi);
         if (d.cnt <= 0) continue;
-        const int kst = tc_stages(*d.pb);
+        const int kst = unit_stages(d);
         for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
             const uint32_t buf = jb & 1u;
-            ok = tc_wait_warp(&acc_empty[buf], ((jb >> 1) & 1u) ^ 1u, abort_flag);
-            if (!ok) break;
-            tc::fence_after_sync();
+            // this warp's stages of the product: g .. g + kst - 1 with g' mod kMmaWarps == mw
+            const uint32_t first = g + (uint32_t)((mw - (int)(g % kMmaWarps) + kMmaWarps) % kMmaWarps);
+            if (first < g + (uint32_t)kst) {
+                ok = tc_wait_warp(&acc_empty[buf], ((jb >> 1) & 1u) ^ 1u, abort_flag);
+                if (!ok) break;
+                tc::fence_after_sync();
+            }
             const uint32_t dt = tmem + buf * kAccCols;
             const uint32_t idesc = tc::idesc_f16_f32(kTcM, npad);
-            for (int ks = 0; ks < kst; ++ks) {
-                const uint32_t as = g % kASlots, bs = g % kBStages;
-                ok = tc_wait_warp(&s_full[as], (g / kASlots) & 1u, abort_flag) &&
-                     tc_wait_warp(&b_full[bs], (g / kBStages) & 1u, abort_flag);
+            for (uint32_t gs = first; gs < g + (uint32_t)kst; gs += kMmaWarps) {
+                const uint32_t as = gs % kStages;
+                ok = tc_wait_warp(&full[as], (gs / kStages) & 1u, abort_flag);
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (lane == 0) {
-                    const uint32_t b0 = sbase + bs * kBStageBytes;
-                    const uint32_t a0 = tmem + kColA + 32u * as;
-#pragma unroll
-                    for (int k16 = 0; k16 < 4; ++k16)
-                        tc::mma_f16_ts(dt, a0 + 8u * k16, tc::sw128_desc(b0, k16), idesc,
-                                       (ks | k16) != 0);
-                    tc::mma_commit(&b_empty[bs]);
-                    tc::mma_commit(&s_empty[as]);
+                    // the delta rows were written by cp.async (generic proxy): make them
+                    // visible to the tensor core's reads
+                    tc::fence_async_smem();
+                    tc::mma4_f16_ts_acc(dt, tmem + kColA + 32u * as,
+                                        tc::sw128_desc(sbase + as * kBStageBytes, 0), idesc);
+                    tc::mma_commit(&empty[as]);
                 }
                 __syncwarp();
                 issued = true;
-                ++g;
             }
             if (!ok) break;
+            // this warp's part of the product is issued (possibly none of it)
             if (lane == 0) tc::mma_commit(&acc_full[buf]);
             __syncwarp();
+            g += (uint32_t)kst;
             ++jb;
         }
     }
     // every product issued has completed before tensor memory is released
     if (issued) {
-        if (lane == 0) tc::mma_commit(done);
+        if (lane == 0) tc::mma_commit(&done[mw]);
         __syncwarp();
-        tc_wait(done, 0u, no_abort);
+        tc_wait(&done[mw], 0u, no_abort);
     }
 }
 
 // ---- epilogue warps ----------------------------------------------------------------------------
 // Warp w reads lane quadrant w mod 4 (patch pixels 32 (w mod 4) ..) and columns 16 (w / 4) ..
 // of every 32-column step.
-__device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
-                            uint64_t *acc_empty, uint32_t tmem, volatile int *abort_flag)
+__device__ void tc_epilogue(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
+                            uint64_t *acc_full, uint64_t *acc_empty, uint32_t tmem,
+                            volatile int *abort_flag)
 {
     const int et = threadIdx.x;  // 0 .. 255
     const int w = et >> 5, lane = et & 31;
     const int quad = w & 3, half = w >> 2;
-    int32_t *dt = reinterpret_cast<int32_t *>(smem + kOffDt);  // [2][32][128] or [kNB][32]
+    int32_t *dt = reinterpret_cast<int32_t *>(smem + kOffDt);  // [32][128] or [kNB][32]
     // per listed pixel, by product parity: (table offset, partner, slot, x | y << 16) and
     // (its patch-local x, y, the partner's patch pixel or -1, slot)
     int4 *colb = reinterpret_cast<int4 *>(smem + kOffCol);
     int4 *col1b = colb + 2 * kNB;
+    int32_t *acc6 = reinterpret_cast<int32_t *>(smem + kOffAcc6);  // [kNB][kAccStride]
     int32_t *tab = reinterpret_cast<int32_t *>(smem + kOffTab);
     int8_t *tab2 = reinterpret_cast<int8_t *>(smem + kOffTab2);
     const int row = 32 * quad + lane;  // the patch pixel of this thread's accumulator lane
     const int lx = row & 15, ly = row >> 4;
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-    uint32_t jb = 0, ci = 0;
+    uint32_t jb = 0;
     int cur = -1;
+    int32_t *tc_cnt = nullptr;  // the current problem's list counts
     bool ok = true;
-    for (int u = blockIdx.x; u < args.total_units && ok; u += gridDim.x) {
+    for (int ku = 0; ku < nu && ok; ++ku) {
         int pi;
-        const Unit d = decode_unit(args, u, pi);
+        const Unit d = unit_at(utab, ku, pi);
         if (d.cnt <= 0) continue;
-        const Problem &pb = *d.pb;
-        const int W = pb.W, H = pb.H, hw = W >> 1, hh = H >> 1;
-        const int r = pb.radius, r2 = r * r, ncls = pb.n_cls;
-        const bool fast = tab2_ok(W, H, r);
+        const int W = unit_w(d), H = unit_h(d), hw = W >> 1, hh = H >> 1;
+        const int r = (d.t->nr >> 16) & 0xFF, r2 = r * r, ncls = d.t->nr >> 24;
+        const bool fast = (d.t->flags & kUnitTable) != 0;
         const int tw = tab2_w(r);
         // compile-time path: radius 6 with the classes of the static stencil
-        const bool colpath = fast && r == 6 && ncls == kCls6 &&
-                             classes_match6(pb.d2, std::make_integer_sequence<int, kCls6>{});
+        const bool colpath = (d.t->flags & kUnitStatic6) != 0;
         if (pi != cur) {  // class of each squared distance / offset of this problem
+            const Problem &pb = args.probs[pi];
             epi_sync();
             for (int i = et; i < kTabMax; i += kEpiThreads) tab[i] = -1;
             epi_sync();
@@ -721,14 +825,15 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
                 epi_sync();
             }
             cur = pi;
+            tc_cnt = pb.tc_cnt;
         }
         const int qx = d.x0 + lx, qy = d.y0 + ly;
         const bool qin = qx < W && qy < H;
         const int qpix = qy * W + qx;
         // this lane's part of the 2-D table index (offsets from the patch centre)
         const int lt = (ly - kPH / 2 + tab2_dy(r)) * tw + (lx - kPW / 2 + tab2_dx(r));
-        int32_t *const side = pb.side_cls;
-        const int4 *list = pb.tc_list + (size_t)d.pid * pb.tc_cap;
+        int32_t *const side = d.t->side;
+        const int4 *list = d.t->list;
         for (int n0 = 0; n0 < d.cnt; n0 += kNB) {
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
@@ -760,13 +865,20 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
                 const int c0 = 32 * k, cc = c0 + 16 * half;  // this warp's first column
                 const bool have = cc < npad;                 // uniform per warp
                 uint32_t v[16];
-                if (have) tc::tmem_ld16(tmem + lane_base + buf * kAccCols + (uint32_t)cc, v);
+                if (have) {  // read, and leave zeros for the next product on this accumulator
+                    const uint32_t ta = tmem + lane_base + buf * kAccCols + (uint32_t)cc;
+                    tc::tmem_ld16(ta, v);
+                    tc::tmem_zero16(ta);
+                }
                 if (k == nch - 1) {  // the accumulator is free once every lane has read it
                     tc::fence_before_sync();
                     mbar_arrive(&acc_empty[buf]);
                 }
                 if (colpath) {
-                    int32_t *dtb = dt + (ci & 1u) * (32 * kTcM);
+                    int32_t *dtb = dt;
+                    // the previous step's readers are done before the transpose is overwritten
+                    // (a product's first step follows the previous product's final barrier)
+                    if (k > 0) epi_sync();
                     if (have) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
@@ -775,8 +887,7 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
                     }
                     epi_sync();
                     const int n = c0 + lane;
-                    if (n < nn) g6_warp(w, dtb + lane * kTcM, col1[n], lane, side);
-                    ++ci;
+                    if (n < nn) g6_warp(w, dtb + lane * kTcM, col1[n], lane, acc6 + n * kAccStride);
                 } else if (have && qin && fast) {
                     // per column: the table lookup, then the class-sum update
 #pragma unroll
@@ -812,7 +923,10 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
                     }
                 }
             }
-            if (!colpath) {
+            if (colpath) {  // the product's class sums
+                epi_sync();
+                g6_flush(acc6, col1, nn, w, lane, side);
+            } else {
                 // warp w sends the class sums of columns w, w + 8, ...; lane = class
                 epi_sync();
                 for (int nb = w; nb < nn; nb += kEpiWarps * kFlushBatch) {
@@ -833,7 +947,7 @@ __device__ void tc_epilogue(const TcArgs &args, char *smem, uint64_t *acc_full,
             ++jb;
         }
         if (!ok) break;
-        if (et == 0) pb.tc_cnt[d.pid] = 0;  // cleared for the next pass
+        if (et == 0) tc_cnt[d.pid] = 0;  // cleared for the next pass
     }
 }
 
@@ -843,31 +957,59 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
     char *smem = reinterpret_cast<char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);
     uint64_t *a_full = bars, *a_empty = a_full + kABoxes;
-    uint64_t *s_full = a_empty + kABoxes, *s_empty = s_full + kASlots;
-    uint64_t *b_full = s_empty + kASlots, *b_empty = b_full + kBStages;
-    uint64_t *acc_full = b_empty + kBStages, *acc_empty = acc_full + 2, *done = acc_empty + 2;
+    uint64_t *full = a_empty + kABoxes, *empty = full + kStages;
+    uint64_t *acc_full = empty + kStages, *acc_empty = acc_full + 2;
+    uint64_t *done = acc_empty + 2;  // [kMmaWarps]
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kOffMisc);
     volatile int *s_abort = reinterpret_cast<volatile int *>(smem + kOffMisc + 4);
     volatile int *s_zero = reinterpret_cast<volatile int *>(smem + kOffMisc + 8);  // stays 0
     const int warp = threadIdx.x >> 5;
+    // this CTA's patches: static part from the plan, listed pixels of this pass
+    TcUnit *utab = reinterpret_cast<TcUnit *>(smem + kOffUnits);
+    const int ufirst = args.unit_begin + blockIdx.x * args.per;
+    const int ulast = min(ufirst + args.per, args.unit_begin + args.unit_count);
+    const int nu = ulast > ufirst ? ulast - ufirst : 0;
+    for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+        const int4 ui = args.units[ufirst + k];
+        const Problem &pb = args.probs[ui.x];
+        int c = 0;
+        if (pb.ctr[0] < pb.ctr[1]) {
+            c = pb.tc_cnt[ui.y];
+            c = c < pb.tc_cap ? c : pb.tc_cap;
+        }
+        TcUnit t;
+        t.pi = ui.x;
+        t.pid = ui.y;
+        t.cnt = c;
+        t.xy = ui.z | (ui.w << 16);
+        t.wh = pb.W | (pb.H << 16);
+        t.geom = pb.row_bytes | (pb.count_bytes << 16);
+        t.nr = pb.N | (pb.radius << 16) | (pb.n_cls << 24);
+        t.M = pb.M;
+        t.list = pb.tc_list + (size_t)ui.y * pb.tc_cap;
+        t.delta = pb.tc_delta16;
+        t.side = pb.side_cls;
+        const bool fast = tab2_ok(pb.W, pb.H, pb.radius);
+        const bool st6 = fast && pb.radius == 6 && pb.n_cls == kCls6 &&
+                         classes_match6(pb.d2, std::make_integer_sequence<int, kCls6>{});
+        t.flags = (fast ? kUnitTable : 0) | (st6 ? kUnitStatic6 : 0);
+        t.pad = 0;
+        utab[k] = t;
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < kABoxes; ++i) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], kConvWarps);
         }
-        for (int i = 0; i < kASlots; ++i) {
-            mbar_init(&s_full[i], kConvWarps);
-            mbar_init(&s_empty[i], 1);
-        }
-        for (int i = 0; i < kBStages; ++i) {
-            mbar_init(&b_full[i], kProdWarps);
-            mbar_init(&b_empty[i], 1);
+        for (int i = 0; i < kStages; ++i) {  // a stage is full when both operands are in
+            mbar_init(&full[i], kConvWarps + kProdThreads);
+            mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_full[i], kMmaWarps);
             mbar_init(&acc_empty[i], kEpiThreads);
         }
-        mbar_init(done, 1);
+        for (int i = 0; i < kMmaWarps; ++i) mbar_init(&done[i], 1);
         *s_abort = 0;
         *s_zero = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -880,17 +1022,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
+    // both accumulators start at zero (every product accumulates onto them; the epilogue
+    // zeroes what it reads)
+    if (warp < kEpiWarps) {
+        const uint32_t q = (uint32_t)(32 * (warp & 3)) << 16;
+        for (uint32_t c = 16u * (warp >> 2); c < 2 * kAccCols; c += 32u) tc::tmem_zero16(tmem + q + c);
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+    tc::fence_after_sync();
     if (warp < kConvWarp0)
-        tc_epilogue(args, smem, acc_full, acc_empty, tmem, s_abort);
+        tc_epilogue(args, utab, nu, smem, acc_full, acc_empty, tmem, s_abort);
     else if (warp < kProdWarp0)
-        tc_convert(args, smem, a_full, a_empty, s_full, s_empty, tmem, s_abort);
+        tc_convert(args, utab, nu, smem, a_full, a_empty, full, empty, tmem, s_abort);
     else if (warp < kLoadWarp)
-        tc_produce_b(args, smem, b_full, b_empty, s_abort);
+        tc_produce_b(args, utab, nu, smem, full, empty, s_abort);
     else if (warp == kLoadWarp) {
-        if ((threadIdx.x & 31) == 0) tc_load_a(args, smem, a_full, a_empty, s_abort, s_zero);
+        if ((threadIdx.x & 31) == 0)
+            tc_load_a(args, utab, nu, smem, a_full, a_empty, s_abort, s_zero);
     } else
-        tc_mma(args, smem, s_full, s_empty, b_full, b_empty, acc_full, acc_empty, done, tmem,
-               s_abort, s_zero);
+        tc_mma(args, utab, nu, smem, full, empty, acc_full, acc_empty, done, tmem, s_abort, s_zero);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -905,18 +1056,55 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
 constexpr int kListThreads = 256;
 constexpr int kMaxMet = 5;  // distinct patch columns (rows) within a radius <= 8 of a pixel
 
+// patch i met at |offset| ad: a new entry, or a smaller offset for a known one (fully unrolled,
+// so the small arrays stay in registers)
 __device__ __forceinline__ void note_patch(int (&idx)[kMaxMet], int (&dist)[kMaxMet], int &n,
                                            int i, int ad)
 {
-    for (int k = 0; k < n; ++k)
-        if (idx[k] == i) {
+    bool found = false;
+#pragma unroll
+    for (int k = 0; k < kMaxMet; ++k)
+        if (k < n && idx[k] == i) {
             dist[k] = ad < dist[k] ? ad : dist[k];
-            return;
+            found = true;
         }
-    if (n < kMaxMet) {
-        idx[n] = i;
-        dist[n] = ad;
+    if (!found && n < kMaxMet) {
+#pragma unroll
+        for (int k = 0; k < kMaxMet; ++k)
+            if (k == n) {
+                idx[k] = i;
+                dist[k] = ad;
+            }
         ++n;
+    }
+}
+__device__ __forceinline__ int pick(const int (&a)[kMaxMet], int i)
+{
+    int v = a[0];
+#pragma unroll
+    for (int k = 1; k < kMaxMet; ++k) v = i == k ? a[k] : v;
+    return v;
+}
+
+// Distinct patches (of size ps along an axis of n pixels) met by the window [c - r, c + r],
+// torus-wrapped (r < n), with the smallest |offset| reaching each.  The window is walked in runs
+// of pixels of one patch (at most four for r <= 8); a run can meet a patch met before when the
+// window wraps on a narrow torus, so every run is merged into the list.
+__device__ __forceinline__ void axis_patches(int c, int r, int n, int ps, int (&idx)[kMaxMet],
+                                             int (&dist)[kMaxMet], int &cnt)
+{
+    const int total = 2 * r + 1;
+    int x = wrap_add(c, -r, n), done = 0;  // window offsets covered so far: done - r ..
+    while (done < total) {
+        const int pc = x / ps;
+        const int cend = (pc + 1) * ps < n ? (pc + 1) * ps : n;
+        const int len = cend - x < total - done ? cend - x : total - done;
+        const int d0 = done - r, d1 = done + len - 1 - r;  // offsets of the run
+        const int a0 = d0 < 0 ? -d0 : d0, a1 = d1 < 0 ? -d1 : d1;
+        note_patch(idx, dist, cnt, pc, (d0 <= 0 && d1 >= 0) ? 0 : (a0 < a1 ? a0 : a1));
+        done += len;
+        x += len;
+        x -= x >= n ? n : 0;
     }
 }
 
@@ -986,22 +1174,20 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
     const int r = pb.radius, r2 = r * r;
     const int p = side ? b : a, px = p % pb.W, py = p / pb.W;
     // distinct patch columns (rows) met by x in [px - r, px + r] (y likewise), torus-wrapped,
-    // with the smallest |offset| that reaches each (a walk can leave a patch and come back
-    // to it on a narrow torus, so every earlier entry is checked)
+    // with the smallest |offset| that reaches each
     int xi[kMaxMet], xd[kMaxMet], yi[kMaxMet], yd[kMaxMet], nx = 0, ny = 0;
-    for (int dd = -r; dd <= r; ++dd) {
-        const int ad = dd < 0 ? -dd : dd;
-        note_patch(xi, xd, nx, wrap_add(px, dd, pb.W) / kPW, ad);
-        note_patch(yi, yd, ny, wrap_add(py, dd, pb.H) / kPH, ad);
-    }
+    axis_patches(px, r, pb.W, kPW, xi, xd, nx);
+    axis_patches(py, r, pb.H, kPH, yi, yd, ny);
     // at most 3 x 4 patches for radius <= 8; the loop covers any count
     for (int kk = k; kk < nx * ny; kk += 16) {
         const int u = kk / ny, w = kk - (kk / ny) * ny;  // this lane's patch
-        if (xd[u] * xd[u] + yd[w] * yd[w] <= r2) {  // in reach
-            const int pid = yi[w] * pb.tc_npx + xi[u];
+        const int xdu = pick(xd, u), ydw = pick(yd, w);
+        if (xdu * xdu + ydw * ydw <= r2) {  // in reach
+            const int xiu = pick(xi, u), yiw = pick(yi, w);
+            const int pid = yiw * pb.tc_npx + xiu;
             const int pos = atomicAdd(pb.tc_cnt + pid, 1);
             // min-image offset of p from the patch centre
-            int rx = px - (xi[u] * kPW + kPW / 2), ry = py - (yi[w] * kPH + kPH / 2);
+            int rx = px - (xiu * kPW + kPW / 2), ry = py - (yiw * kPH + kPH / 2);
             rx -= rx > (pb.W >> 1) ? pb.W : 0;
             rx += rx < -(pb.W >> 1) ? pb.W : 0;
             ry -= ry > (pb.H >> 1) ? pb.H : 0;
@@ -1030,11 +1216,21 @@ __global__ void __launch_bounds__(kListThreads) k_tc_finalize(const Problem *pro
         float dL = 0.f, S = 0.f;
         uint8_t flags = 0;
         if (a < pb.P && b < pb.P) {
-            const int32_t *ca = pb.side_cls + (size_t)j * 2 * kMaxClasses;
-            const int32_t *cb = ca + kMaxClasses;
+            // the two sides' class sums: two 128-byte rows, read as 16-byte vectors
+            const int4 *ca = reinterpret_cast<const int4 *>(pb.side_cls +
+                                                            (size_t)j * 2 * kMaxClasses);
+            const int4 *cb = ca + kMaxClasses / 4;
             int A[kMaxClasses];
 #pragma unroll
-            for (int c = 0; c < kMaxClasses; ++c) A[c] = c < pb.n_cls ? ca[c] + cb[c] : 0;
+            for (int v = 0; v < kMaxClasses / 4; ++v) {
+                const int4 x = ca[v], y = cb[v];
+                A[4 * v + 0] = x.x + y.x;
+                A[4 * v + 1] = x.y + y.y;
+                A[4 * v + 2] = x.z + y.z;
+                A[4 * v + 3] = x.w + y.w;
+            }
+#pragma unroll
+            for (int c = 0; c < kMaxClasses; ++c) A[c] = c < pb.n_cls ? A[c] : 0;
             couple_delta(pb, A, dL, S);
             const bool improving = (float)pb.objective * dL < 0.f;
             const bool tie = fabsf(dL) < 1e-6f * S;
@@ -1127,12 +1323,18 @@ cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm
     k_tc_lists<<<gw, kListThreads, 0, st>>>(tl.dprob);
     if (all) tm->end(st);
     if (tl.total_units > 0) {
-        const TcArgs a{tl.dprob, tl.n_prob, tl.unit_start, tl.total_units, tl.tmaps};
-        const int grid = tl.total_units < tl.sms ? tl.total_units : tl.sms;
+        // each CTA takes a contiguous run of at most kUnitTab patches; a pass with more
+        // patches than the SMs hold that way is split over several launches
+        int per = (tl.total_units + tl.sms - 1) / tl.sms;
+        per = per < kUnitTab ? per : kUnitTab;
         if (timed) tm->begin(kKTcStencil, st);
-        k_tc_stencil<<<grid, kTcThreads, kSmemBytes, st>>>(a);
+        for (int b0 = 0; b0 < tl.total_units; b0 += per * tl.sms) {
+            const int cnt = tl.total_units - b0 < per * tl.sms ? tl.total_units - b0 : per * tl.sms;
+            const TcArgs a{tl.dprob, tl.n_prob, tl.units, b0, cnt, per, tl.tmaps};
+            k_tc_stencil<<<(cnt + per - 1) / per, kTcThreads, kSmemBytes, st>>>(a);
+            note_launches(1);
+        }
         if (timed) tm->end(st);
-        note_launches(1);
     }
     if (all) tm->begin(kKTcFinalize, st);
     k_tc_finalize<<<gl, kListThreads, 0, st>>>(tl.dprob);
