@@ -78,18 +78,26 @@ def all_reduce_list(values, dist, device: str, op: str = "max") -> list[float]:
 
 
 def merge_serving(summary: dict, dist, device: str) -> dict:
-    """Whole-job serving figures: worst rank's latencies and makespan, summed work."""
-    if dist is None:
-        return summary
-    keys = ("p50_latency_s", "p99_latency_s", "p99_queue_s", "makespan_s")
-    out = dict(summary)
-    for k, v in zip(keys, all_reduce_list([summary[k] for k in keys], dist, device, "max")):
-        out[k] = v
-    props, done = all_reduce_list([summary["proposals_per_s"] * summary["makespan_s"],
-                                   summary["completed"]], dist, device, "sum")
-    out["proposals_per_s"] = props / out["makespan_s"]
-    out["served_req_per_s"] = done / out["makespan_s"]
-    out["completed"] = int(done)
+    """Whole-job serving figures: latency percentiles of every rank's requests pooled (the
+    per-request latencies are all-gathered), the slowest rank's makespan, summed work and
+    request counts.  The raw per-request lists are dropped from the result."""
+    from paper_2105_12620_gb300 import serving as srv
+    out = {k: v for k, v in summary.items() if k not in ("latencies_s", "queue_s")}
+    lat, wait = list(summary.get("latencies_s", [])), list(summary.get("queue_s", []))
+    if dist is not None:
+        gathered = [None] * dist.get_world_size()
+        dist.all_gather_object(gathered, (lat, wait))
+        lat = [v for g in gathered for v in g[0]]
+        wait = [v for g in gathered for v in g[1]]
+        (out["makespan_s"],) = all_reduce_list([summary["makespan_s"]], dist, device, "max")
+        props, done, reqs = all_reduce_list(
+            [summary["proposals_per_s"] * summary["makespan_s"], summary["completed"],
+             summary["requests"]], dist, device, "sum")
+        out["proposals_per_s"] = props / out["makespan_s"]
+        out["served_req_per_s"] = done / out["makespan_s"]
+        out["completed"], out["requests"] = int(done), int(reqs)
+    out.update(srv.latency_percentiles(lat, wait))
+    out["latency_samples"] = len(lat)
     return out
 
 
@@ -266,7 +274,8 @@ def plain_per_tile(pkg, stream, rank, sweeps: int = 512, reps: int = 3) -> dict:
 def run_serving(pkg, args, rank: int, local: int, world: int, dist, n_requests: int | None = None,
                 rate: float | None = None) -> dict:
     """Bounded run of the serving loop: a Poisson stream of mixed requests per GPU (weak
-    scaling: every rank serves its own stream); latencies are the worst rank's."""
+    scaling: every rank serves its own stream); latency percentiles pool every rank's
+    requests."""
     from paper_2105_12620_gb300 import serving as srv
 
     n_requests = args.serving_requests if n_requests is None else n_requests
@@ -282,7 +291,9 @@ def run_serving(pkg, args, rank: int, local: int, world: int, dist, n_requests: 
                   "requests (bounded run), side log-uniform 32..512, N in {16,64,256}, T=1024, "
                   "1 or 2 pairs, pass budget uniform 500..5000",
         "max_slots": args.serving_slots, "sweeps_per_chunk": args.serving_chunk,
-        "memory_budget": "80% of free device memory", "latency": "submit to done"}
+        "memory_budget": "80% of free device memory", "latency": "submit to done",
+        "schedule": "tensor-core batch for the request signatures the autotuner assigns to it "
+                    "(timed once per signature), the other requests fused in a second batch"}
     return summary
 
 
@@ -391,6 +402,68 @@ def kernel_roofline(ktimes: dict, specs, split_steps: int, sweeps: int, args, ch
                      "(152 SMs x 64/clk x 4 x 2.07 GHz)"),
             "launches": nl, "avg_launch_ms": tms / nl, "share": tms / max(all_ms, 1e-9),
             "hbm": hbm}
+
+
+def run_extra_workload(pkg, args, name: str, stream, rank: int, world: int, dist) -> dict:
+    """One more workload timed like the headline (autotuned schedule, CUDA-graph sweeps, L2
+    flushed between steps, device events around each step), reported beside it: the 256 x 256
+    two-pair tile with int16 counts (c3) or the 96 mixed tiles (c4)."""
+    import torch
+
+    sub = argparse.Namespace(**vars(args))
+    sub.workload, sub.sweeps = name, 0
+    specs, desc = workload_tiles(sub)
+    B = len(specs)
+    sweeps = specs[0].sweeps
+    tiles = [pkg.Sampler(t.width, t.height, t.n_points, t.n_integrands,
+                         seed=tile_seed(rank, 0, i, B), n_pairs=t.n_pairs, sigma=SIGMA,
+                         radius=RADIUS, stream=stream)
+             for i, t in enumerate(specs)]
+    batch = pkg.Batch(tiles, stream=stream) if B > 1 else None
+    chosen = batch.autotune(20) if batch is not None else tiles[0].autotune(20)
+    energy_dev = torch.empty(sum(t.n_pairs for t in specs), dtype=torch.float64, device="cuda")
+    energy_off = [0]
+    for t in specs:
+        energy_off.append(energy_off[-1] + t.n_pairs)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(k: int):
+        for i, t in enumerate(tiles):
+            t.reset(tile_seed(rank, k, i, B))
+        (batch if batch is not None else tiles[0]).optimize(sweeps, stats=False)
+        for i, t in enumerate(tiles):
+            t.energy_into(energy_dev[energy_off[i]:energy_off[i + 1]].data_ptr())
+
+    steps = args.extra_steps
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            flush.zero_()
+            step(k)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    (total_ms,) = all_reduce_list([sum(a.elapsed_time(b) for a, b in ev)], dist, "cuda", "max")
+    if batch is not None:
+        batch.close()
+    for t in tiles:
+        t.close()
+    props = sum(t.proposals() for t in specs)
+    return {"value": world * props * steps / (total_ms / 1000.0), "unit": UNIT,
+            "tiles_per_s": world * B * steps / (total_ms / 1000.0),
+            "ms_per_step": total_ms / steps, "steps": steps, "warmup": args.warmup,
+            "dtype": "int16" if any(t.n_points > 64 for t in specs) else "int8",
+            "config": {"workload": desc, "tiles_per_gpu": B, "sweeps": sweeps,
+                       "schedule": schedule_desc(chosen),
+                       "timing": "device events around each step; sweeps replayed from CUDA "
+                                 "graphs; L2 flushed between steps (256 MB write)"}}
 
 
 def run_ours(args) -> int:
@@ -528,6 +601,11 @@ def run_ours(args) -> int:
     plain = None
     if not args.no_plain and rank == 0 and args.workload == "c2":
         plain = plain_per_tile(pkg, stream, rank)
+    extra = {}
+    if args.workload == "c2":
+        for name in args.extra_workloads.split(","):
+            if name:
+                extra[name] = run_extra_workload(pkg, args, name, stream, rank, world, dist)
     serving = serving_light = None
     if args.serving_requests > 0 and args.workload == "c2":
         serving = run_serving(pkg, args, rank, local, world, dist)
@@ -575,6 +653,8 @@ def run_ours(args) -> int:
             "serving": serving,
             "serving_light": serving_light,
         }
+        for name, res in extra.items():
+            line["workload_" + name] = res
         print(json.dumps(line), flush=True)
     if batch is not None:
         batch.close()
@@ -717,7 +797,12 @@ def main(argv=None) -> int:
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--spw", type=int, default=4)
     ap.add_argument("--tsplit", type=int, default=1)
-    ap.add_argument("--serving-requests", type=int, default=64,
+    ap.add_argument("--extra-workloads", default="c3,c4",
+                    help="workloads timed after the headline and reported beside it (c3, c4; "
+                         "empty skips them)")
+    ap.add_argument("--extra-steps", type=int, default=2,
+                    help="timed steps of each extra workload (warm-up: --warmup)")
+    ap.add_argument("--serving-requests", type=int, default=500,
                     help="requests of the bounded serving run (0 skips it)")
     ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrivals/s")
     ap.add_argument("--serving-slots", type=int, default=64)

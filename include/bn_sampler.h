@@ -65,7 +65,7 @@ extern "C" {
 #define BN_SCHEDULE_PERSISTENT 2 /* one cooperative launch for many sweeps, SMEM-blocked    */
 #define BN_SCHEDULE_TENSOR 3     /* five launches per sweep, the stencil of Eq. 1 as products */
                                  /* on the 5th-generation tensor cores (N <= 512 and         */
-                                 /* T N^2 <= 2^25, tile sides >= 2 radius + 1)               */
+                                 /* radius <= 8, tile sides >= 2 radius + 1)                 */
 
 typedef struct bn_config {
     int32_t width, height;     /* toroidal tile, 2..4096 each, width*height <= 2^22          */
@@ -199,15 +199,14 @@ int bn_kernel_times(bn_sampler *s, bn_kernel_time *out, int32_t cap, int32_t *n_
 /* ---- execution schedule (speed only; results do not depend on it) ------------------------ */
 /* kind: BN_SCHEDULE_*.  For the persistent kernel, block_x x block_y pixels per work unit,
  * threads per CTA and proposed pixels per compute warp per round must name an instantiated
- * shape (8x8/256/4, 16x8/512/4, 8x16/512/4, 8x8/512/4; a shape that does not fit the
- * tiles gives way to the first one that does); tsplit = chunk ranges per block
- * (1..4, 0 = auto).  8x8/512/4 evaluates 8-bit counts on the tensor cores (mma.sync f16, exact
- * for N <= 64) and needs tile sides that are multiples of 8, at least 24.  block_x = 0 keeps the
- * default shape.  BN_SCHEDULE_TENSOR ignores the other fields; for every problem it needs counts
- * below 1024 (N <= 512), centred products that stay exact in f32 (T N^2 <= 2^25), radius <= 8
- * and tile sides of at least 2 radius + 1 (BN_ERR_INVALID_ARG otherwise); its plan holds the
- * couples' per-pass f16 deltas (1/4 of the count bytes for 8-bit counts, 1/8 for 16-bit) and one
- * TMA tensor map per problem, released with the plan.  set synchronises the stream. */
+ * shape (8x8/256/4, 16x8/512/4, 8x16/512/4; a shape that does not fit the tiles, i.e. tiles
+ * narrower than block_x + 2 radius, gives way to the first one that does); tsplit = chunk
+ * ranges per block (1..4, 0 = auto).  block_x = 0 keeps the default shape.
+ * BN_SCHEDULE_TENSOR ignores the other fields; for every problem it needs counts below 1024
+ * (N <= 512), radius <= 8 and tile sides of at least 2 radius + 1 (BN_ERR_INVALID_ARG
+ * otherwise); the centred products are summed exactly in f32 per accumulator round of at most
+ * 2^25 / (64 N^2) stages of 64 integrands, the rounds as integers; its plan holds the couples' per-pass f16 deltas (1/4 of the count bytes for 8-bit counts, 1/8 for 16-bit) and one TMA
+ * tensor map per problem, released with the plan.  set synchronises the stream. */
 typedef struct bn_schedule {
     int32_t kind;
     int32_t block_x, block_y;
@@ -294,7 +293,11 @@ void bn_batch_destroy(bn_batch *b);
  * budget.  The thread admits queued requests (first come, first served) while a slot is free and
  * their device memory fits the budget, initialises their samplers on a side stream, sweeps all
  * resident requests together in fused batches of at most sweeps_per_chunk passes each (each
- * request stops at its own budget inside the launch), and retires finished ones (final Eq. 1 and
+ * request stops at its own budget inside the launch): one batch on the tensor-core schedule for
+ * the requests whose signature (count width, N, T, radius, pairs, tile sides rounded up to
+ * powers of two) the autotuner assigned to it, timed once per signature on a scratch copy of the
+ * first such request and cached for the server's lifetime, and one batch for the rest.  It
+ * retires finished requests (final Eq. 1 and
  * the optimised shifts copied to host, device memory released).  A request's result is identical
  * to running it alone through bn_sampler_init + bn_optimize_sweeps with the same pass budget.
  * All functions are thread-safe; none waits for the GPU except bn_server_drain/destroy. */
@@ -304,9 +307,13 @@ typedef struct bn_server_config {
     int32_t device;               /* CUDA device index                                       */
     int32_t max_slots;            /* resident requests at most (1..4096)                     */
     int32_t sweeps_per_chunk;     /* passes per fused launch sequence (1..500)               */
-    int32_t reserved;
+    int32_t tensor_policy;        /* BN_SERVE_TENSOR_*: which requests join the tensor batch */
     int64_t memory_budget_bytes;  /* device bytes for resident requests; 0 = 80% of free     */
 } bn_server_config;
+
+#define BN_SERVE_TENSOR_TUNED 0   /* the autotuner's choice per request signature (default)  */
+#define BN_SERVE_TENSOR_ALWAYS 1  /* every request that supports the schedule, no trials     */
+#define BN_SERVE_TENSOR_NEVER 2   /* none: one fused batch on the other schedules            */
 
 typedef struct bn_request {
     bn_config cfg;                /* the sampler to build (schedule is ignored)              */
@@ -329,6 +336,8 @@ typedef struct bn_server_stats {
     int64_t chunks;               /* fused launch sequences run                              */
     int64_t proposals;            /* couples proposed (pairs x couples x passes)             */
     int64_t memory_in_use, memory_budget;
+    int64_t tensor_chunks;        /* chunks that ran a batch on the tensor-core schedule     */
+    int64_t tunes;                /* request signatures timed by the autotuner               */
 } bn_server_stats;
 
 int bn_server_create(const bn_server_config *cfg, bn_server **out);

@@ -21,6 +21,7 @@ BN_MODE_NONINTERACTING, BN_MODE_CONCURRENT = 0, 1
 BN_OBJECTIVE_BLUE, BN_OBJECTIVE_LITERAL = -1, 1
 BN_SCHEDULE_AUTO, BN_SCHEDULE_PLAIN, BN_SCHEDULE_PERSISTENT, BN_SCHEDULE_TENSOR = 0, 1, 2, 3
 BN_INTEGRANDS_HEAVISIDE, BN_INTEGRANDS_GAUSSIAN = 0, 1
+BN_SERVE_TENSOR_TUNED, BN_SERVE_TENSOR_ALWAYS, BN_SERVE_TENSOR_NEVER = 0, 1, 2
 
 
 class BnConfig(ctypes.Structure):
@@ -63,7 +64,7 @@ class BnSchedule(ctypes.Structure):
 
 class BnServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32),
-                ("sweeps_per_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sweeps_per_chunk", ctypes.c_int32), ("tensor_policy", ctypes.c_int32),
                 ("memory_budget_bytes", ctypes.c_int64)]
 
 
@@ -83,13 +84,12 @@ class BnResult(ctypes.Structure):
 class BnServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "submitted", "admitted", "completed", "rejected", "cancelled", "failed", "pending",
-        "active", "chunks", "proposals", "memory_in_use", "memory_budget")]
+        "active", "chunks", "proposals", "memory_in_use", "memory_budget", "tensor_chunks",
+        "tunes")]
 
 
-# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, pixels/warp);
-# (8, 8, 512, 4) is the tensor-core variant for 8-bit counts on tiles of width 8k >= 24
-PERSISTENT_SHAPES = [(8, 8, 256, 4), (16, 8, 512, 4), (8, 16, 512, 4), (8, 8, 512, 4)]
-MMA_SHAPE = (8, 8, 512, 4)
+# CTA shapes instantiated for the persistent kernel: (block_x, block_y, threads, pixels/warp)
+PERSISTENT_SHAPES = [(8, 8, 256, 4), (16, 8, 512, 4), (8, 16, 512, 4)]
 
 
 class BnError(RuntimeError):

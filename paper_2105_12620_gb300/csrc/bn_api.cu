@@ -108,6 +108,7 @@ struct SweepPlan {
     bool tensor = false;            // tensor-core schedule (every problem supports it)
     int4 *d_tc_units = nullptr;     // [tc_units] (problem, patch, x0, y0) of every 16 x 8 patch
     int tc_units = 0;
+    bool tc_rounds = false;         // some problem needs several accumulator rounds
     // the problems as the tensor-core kernels see them: the same state plus the plan's per-pass
     // f16 delta rows (allocations in tc_bufs)
     bn::Problem *d_tcprob = nullptr;
@@ -153,6 +154,7 @@ void free_plan(SweepPlan &pl)
     pl.tensor = false;
     pl.persistent = false;
     pl.tc_units = 0;
+    pl.tc_rounds = false;
     pl.d_prefix = nullptr;
     pl.d_bar = nullptr;
     pl.d_work = nullptr;
@@ -331,12 +333,16 @@ int64_t bn::estimate_device_bytes(const bn_config &c)
 {
     if (validate(c) != BN_OK) return -1;
     Slab sizing;
+    size_t tc_extra = 0;  // a tensor-core plan's delta rows, tensor map and patch table
     for (int i = 0; i < c.n_pairs; ++i) {
         bn::Problem h;
         describe(c, i, h);
         carve(sizing, h);
+        if (bn::tc_supported(h))
+            tc_extra += bn::tc_delta_bytes(h) + (size_t)bn::tc_tensor_map_bytes() +
+                        sizeof(int4) * (size_t)bn::tc_units_per_problem(h) + sizeof(bn::Problem);
     }
-    return (int64_t)(sizing.used + 256 + sizeof(bn::Problem) * c.n_pairs +
+    return (int64_t)(sizing.used + 256 + sizeof(bn::Problem) * c.n_pairs + tc_extra +
                      sizeof(float) * (size_t)c.width * c.height * 2 * c.n_pairs + 4096);
 }
 
@@ -407,7 +413,7 @@ int build_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int
         for (auto &h : hp)
             if (!bn::tc_supported(h))
                 return fail(BN_ERR_INVALID_ARG, "the tensor-core schedule needs counts below "
-                            "1024 (N <= 512), exact centred products (T N^2 <= 2^25), radius "
+                            "1024 (N <= 512), T N^2 <= 2^27 (exact centred products), radius "
                             "<= 8 and tile sides of at least 2 radius + 1");
         std::vector<int4> units;
         for (int i = 0; i < pl.n_prob; ++i)
@@ -415,6 +421,8 @@ int build_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int
                 units.push_back(make_int4(i, pid, (pid % hp[i].tc_npx) * 16,
                                           (pid / hp[i].tc_npx) * 8));
         pl.tc_units = (int)units.size();
+        pl.tc_rounds = false;
+        for (auto &h : hp) pl.tc_rounds = pl.tc_rounds || bn::tc_rounds(h);
         BN_CUDA(bn::prepare_tc());
         pl.tcprob = hp;
         const size_t mb = (size_t)bn::tc_tensor_map_bytes();
@@ -519,16 +527,6 @@ int build_plan(const std::vector<bn::Problem> &hp, const bn::Problem *dprob, int
     BN_CUDA(cudaMemcpy(pl.d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     BN_CUDA(cudaMalloc(&pl.d_bar, sizeof(bn::GridBarrier)));
     BN_CUDA(cudaMalloc(&pl.d_work, 2 * sizeof(int)));
-    if (bn::persistent_shape_is_mma(pl.shape) && pl.count[0] > 0) {
-        // tensor maps of the 8-bit problems' count planes, in problem order
-        const size_t per = (size_t)bn::kTensorMapsPerProblem * bn::kTensorMapBytes;
-        std::vector<char> maps((size_t)pl.n_prob * per, 0);
-        for (int i = 0; i < pl.n_prob; ++i)
-            if (hp[i].count_bytes == 1)
-                BN_CUDA(bn::encode_count_tensor_maps(hp[i], maps.data() + (size_t)i * per));
-        BN_CUDA(cudaMalloc(&pl.d_tmaps, maps.size()));
-        BN_CUDA(cudaMemcpy(pl.d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
-    }
     (void)dprob;
     return BN_OK;
 }
@@ -564,7 +562,7 @@ cudaError_t launch_pass(const SweepPlan &pl, const bn::SweepLaunch &sl, cudaStre
 {
     if (!pl.tensor) return bn::launch_plain_sweep(sl, st, tm);
     const bn::TcLaunch tl{pl.d_tcprob, sl.n_prob, pl.max_M, pl.d_tc_units, pl.tc_units, pl.sms,
-                          pl.d_tmaps};
+                          pl.d_tmaps, pl.tc_rounds};
     return bn::launch_tc_sweep(tl, st, tm);
 }
 
@@ -633,9 +631,6 @@ int run_plan(SweepPlan &pl, const bn::Problem *dprob, const std::vector<bn::Prob
         a.tsplit = pl.shape.tsplit;
         a.bar = pl.d_bar;
         a.work = pl.d_work;
-        a.tmaps = pl.d_tmaps ? pl.d_tmaps + (size_t)pl.first[g] * bn::kTensorMapsPerProblem *
-                                                bn::kTensorMapBytes
-                             : nullptr;
         for (int32_t done = 0; done < n_sweeps; done += kItersPerLaunch) {
             a.n_iter = n_sweeps - done < kItersPerLaunch ? n_sweeps - done : kItersPerLaunch;
             BN_CUDA(cudaMemsetAsync(pl.d_bar, 0, sizeof(bn::GridBarrier), st));
@@ -1461,6 +1456,14 @@ int bn_batch_get_schedule(bn_batch *b, bn_schedule *out)
 // ---- batches ---------------------------------------------------------------------------------
 int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, bn_batch **out)
 {
+    return bn::batch_create_as(samplers, n, cuda_stream, BN_SCHEDULE_AUTO, out);
+}
+
+}  // extern "C"
+
+int bn::batch_create_as(bn_sampler *const *samplers, int32_t n, void *cuda_stream, int schedule,
+                        bn_batch **out)
+{
     bn::TraceRange trace_("bn.batch_create");
     if (!samplers || n <= 0 || !out) return fail(BN_ERR_INVALID_ARG, "bad batch arguments");
     *out = nullptr;
@@ -1494,13 +1497,15 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
         bn_batch_destroy(b);
         return fail(BN_ERR_CUDA, "batch allocation failed: %s", cudaGetErrorString(e));
     }
-    int sched = BN_SCHEDULE_AUTO;
-    bool all_tensor = true;
-    for (int i = 0; i < n; ++i) {
-        if (samplers[i]->cfg.schedule == BN_SCHEDULE_PLAIN) sched = BN_SCHEDULE_PLAIN;
-        all_tensor = all_tensor && samplers[i]->cfg.schedule == BN_SCHEDULE_TENSOR;
+    int sched = schedule;
+    if (sched == BN_SCHEDULE_AUTO) {  // derived from the members' configured schedules
+        bool all_tensor = true;
+        for (int i = 0; i < n; ++i) {
+            if (samplers[i]->cfg.schedule == BN_SCHEDULE_PLAIN) sched = BN_SCHEDULE_PLAIN;
+            all_tensor = all_tensor && samplers[i]->cfg.schedule == BN_SCHEDULE_TENSOR;
+        }
+        if (all_tensor && sched == BN_SCHEDULE_AUTO) sched = BN_SCHEDULE_TENSOR;
     }
-    if (all_tensor && sched == BN_SCHEDULE_AUTO) sched = BN_SCHEDULE_TENSOR;
     b->all = all;
     if (int rc = make_plan(b->all, b->dprob, sched, nullptr, b->plan)) {
         std::string msg = g_error;
@@ -1510,6 +1515,26 @@ int bn_batch_create(bn_sampler *const *samplers, int32_t n, void *cuda_stream, b
     *out = b;
     return BN_OK;
 }
+
+int bn::tune_schedule(bn_sampler *s, int32_t trial_sweeps, bn_schedule *best)
+{
+    if (!s || !best) return fail(BN_ERR_INVALID_ARG, "null argument");
+    if (trial_sweeps < 1 || trial_sweeps > 10000)
+        return fail(BN_ERR_INVALID_ARG, "trial_sweeps must be in [1, 10000]");
+    if (int rc = set_device(s)) return rc;
+    BN_CUDA(cudaStreamSynchronize(s->stream));
+    return autotune({s}, trial_sweeps, s->stream, best);
+}
+
+bool bn::tensor_capable(const bn_sampler *s)
+{
+    if (!s) return false;
+    for (const auto &h : s->hprob)
+        if (!bn::tc_supported(h)) return false;
+    return true;
+}
+
+extern "C" {
 
 int bn_batch_optimize(bn_batch *b, int32_t n_sweeps, bn_sweep_stats *stats)
 {

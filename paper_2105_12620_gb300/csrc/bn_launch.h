@@ -12,8 +12,19 @@
 
 namespace bn {
 
-// device bytes a sampler of this configuration would hold; -1 if the configuration is invalid
+// device bytes a sampler of this configuration would hold, with the tensor-core plan's buffers
+// where the configuration supports that schedule; -1 if the configuration is invalid
 int64_t estimate_device_bytes(const bn_config &c);
+
+// server support (bn_api.cu).  A batch whose plan is built for the given schedule kind
+// (BN_SCHEDULE_AUTO: derived from the members' configured schedules, as bn_batch_create does).
+int batch_create_as(bn_sampler *const *samplers, int32_t n, void *cuda_stream, int schedule,
+                    bn_batch **out);
+// The fastest candidate schedule for one sampler, timed on a scratch copy of its state (its
+// plan, state and pass counter are left as they were); synchronises its stream.
+int tune_schedule(bn_sampler *s, int32_t trial_sweeps, bn_schedule *best);
+// every problem of the sampler supports the tensor-core schedule
+bool tensor_capable(const bn_sampler *s);
 
 // message returned by bn_last_error() on this thread
 void set_last_error(const char *msg);
@@ -85,8 +96,9 @@ cudaError_t launch_set_end(const Problem *dprob, int n_prob, int n_sweeps, int r
 cudaError_t launch_set_ends(const Problem *dprob, int n_prob, const int *n_sweeps_dev,
                             int reset_stats, cudaStream_t st);
 
-// tensor-core schedule (bn_tc.cu): 8-bit counts, or 16-bit counts with N <= 512; centred
-// products exact (T N^2 <= 2^25); radius <= 8; tile sides >= 2 radius + 1
+// tensor-core schedule (bn_tc.cu): 8-bit counts, or 16-bit counts with N <= 512; T N^2 <= 2^27
+// (centred products exact per accumulator round, class sums within int32); radius <= 8; tile
+// sides >= 2 radius + 1
 struct TcLaunch {
     const Problem *dprob;   // device array of problems (each with its tc_delta16 buffer)
     int n_prob;
@@ -95,9 +107,12 @@ struct TcLaunch {
     int total_units;        //   patch, problem by problem
     int sms;
     const char *tmaps;      // device [n_prob] tensor maps of the count planes
+    bool rounds;            // some problem needs more than one accumulator round (tc_rounds)
 };
 bool tc_supported(const Problem &h);
 int tc_units_per_problem(const Problem &h);
+// the problem's integrands are summed in more than one accumulator round (T N^2 > 2^25)
+bool tc_rounds(const Problem &h);
 // bytes of a problem's per-pass f16 delta rows
 size_t tc_delta_bytes(const Problem &h);
 // bytes of one tensor map, and its encoding for a problem's count planes (host)

@@ -16,8 +16,7 @@
 //         A_c(p) += delta_p . k_q  over q in S_c(p),   delta_p = k_partner - k_p,
 //     with the 112 stencil offsets as compile-time shared-memory displacements (one IDP4A per
 //     four 8-bit counts).  The partner's own term is removed and the 18 class sums are reduced
-//     across the warp by a transposing butterfly and stored.  (A tensor-core variant of this
-//     phase, selected by its own CTA shape, is described further down.)
+//     across the warp by a transposing butterfly and stored.
 //   phase 2 (finalize): one thread per couple adds the 2 x tsplit partial class sums, computes
 //     dL in fp32 (compensated), flags and logs it and, if the swap improves the objective,
 //     claims the couple's pixels in the owner grid; it also clears the couple's claims of the
@@ -29,8 +28,6 @@
 // across SMs.  Every wait (grid barrier, mbarrier) has a clock budget; when it runs out the
 // kernel records an error, lets its own copies land (again bounded) and returns.
 #include <utility>
-
-#include <cuda.h>
 
 #include "bn_launch.h"
 #include "bn_persistent.h"
@@ -549,370 +546,6 @@ __device__ void consume_pass(const PersistentArgs &args, char *smem, Pipe &pp,
     }
 }
 
-// ---- tensor-core variant of phase 1 (8-bit counts, tile width a multiple of 8) --------------
-// The unit is an 8 x 8 block; its window is rows y0-6 .. y0+13 and columns x0-8 .. x0+15 (24, so
-// that window columns come in 8-pixel boxes aligned to x = 0 mod 8).  Each chunk of the window
-// arrives by TMA tensor copies of 8 pixels x 128 bytes with the 128-byte swizzle: 16-byte granule
-// g of window pixel (wx, wy) sits at granule position g ^ (wx & 7).  For a round of up to 32
-// proposed pixels the compute warps form
-//     D[s][q] = sum_t delta_s[t] * k_q[t]        (s: proposed pixel, q: window pixel)
-// with mma.sync m16n8k16 on f16 operands: counts and deltas are integers of magnitude <= 64, so
-// the f16 operands and the fp32 sums (< 2^24 for T <= 4096) are exact.  The epilogue adds each
-// D[s][q] whose q lies in the stencil of s (the partner excluded) to the class sum of its squared
-// distance; integer sums, so the result equals the IDP4A variant bit for bit.
-constexpr int kMWinW = 24, kMWinH = 20;             // window columns / rows
-constexpr int kMNcw = 15;                           // compute warps (+ 1 producer)
-constexpr int kMRound = 32;                         // proposed pixels per round (two M-tiles)
-constexpr int kMTiles = kMWinW * kMWinH / 8;        // 60 N-tiles of 8 window pixels
-constexpr int kMTilesPerWarp = kMTiles / kMNcw;     // 4
-constexpr int kMDRow = 144;                         // bytes per delta row: conflict-free fragments
-constexpr int kMCsum = 20;                          // ints per class-sum row
-constexpr int kMMaps = 3;                           // tensor maps per problem (20/14/6 rows)
-constexpr unsigned kMStages = 3;                    // window stages in flight
-static_assert(kMTiles % kMNcw == 0, "N-tiles must split evenly over the compute warps");
-
-// class index of each squared distance 0..36 within the radius-6 stencil (-1: none)
-__constant__ signed char c_cls_of_d2[37] = {-1, 0,  1,  -1, 2,  3,  -1, -1, 4,  5,  6,  -1, -1,
-                                            7,  -1, -1, 8,  9,  10, -1, 11, -1, -1, -1, -1, 12,
-                                            13, -1, -1, 14, -1, -1, 15, -1, 16, -1, 17};
-
-struct SlotM {
-    int wx, wy;     // window position of the pixel
-    int j, side;    // couple and side
-    int p;          // the pixel
-    int partner;    // partner pixel
-    int pdx, pdy;   // min-image offset of the partner if it lies within the radius, else 99
-};
-
-struct MCfg {
-    static constexpr int NT = (kMNcw + 1) * 32;
-    static constexpr int STAGE = kMWinW * kMWinH * kChunk;             // 61 440
-    static constexpr int MAXSLOT = 64;
-    static constexpr int OFF_DELTA = kMStages * STAGE;
-    static constexpr int OFF_CSUM = OFF_DELTA + kMStages * kMRound * kMDRow;
-    static constexpr int OFF_SLOTS = OFF_CSUM + 2 * kMRound * kMCsum * 4;
-    static constexpr int OFF_HDR = OFF_SLOTS + 2 * MAXSLOT * (int)sizeof(SlotM);
-    static constexpr int OFF_BAR = (OFF_HDR + 2 * (int)sizeof(UnitHdr) + 63) / 64 * 64;
-    // full, empty, dfull (one per stage), sfull, sempty, epi (two each)
-    static constexpr int NBAR = 3 * kMStages + 6;
-    // + 1024 so that the stages can start on a 1024-byte boundary (the swizzle atom)
-    static constexpr size_t SMEM = (size_t)OFF_BAR + NBAR * 8 + 1024;
-};
-
-struct MPipe {
-    uint64_t *full, *empty, *sfull, *sempty, *dfull, *epi;
-    unsigned g, ub, rb, issued;
-};
-
-// byte offset of window pixel (wx, wy) in a stage: column blocks of 8 pixels, [block][row][8]
-__device__ __forceinline__ int mwin_off(int wx, int wy)
-{
-    return (((wx >> 3) * kMWinH + wy) * 8 + (wx & 7)) * kChunk;
-}
-
-__device__ __forceinline__ void tma_load_4d(void *dst, const char *tmap, int c0, int c1, int c2,
-                                            int c3, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// four unsigned bytes -> two f16x2 of their values (bytes 0,1 and bytes 2,3); bias: the value
-// added before (0 for counts, 128 for deltas shifted to unsigned)
-__device__ __forceinline__ void bytes_to_h2(uint32_t x, uint32_t bias2, uint32_t &lo, uint32_t &hi)
-{
-    // 0x64XX as f16 is 1024 + XX exactly
-    const uint32_t a = __byte_perm(x, 0x64646464u, 0x4140);
-    const uint32_t b = __byte_perm(x, 0x64646464u, 0x4342);
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(lo) : "r"(a), "r"(bias2));
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(hi) : "r"(b), "r"(bias2));
-}
-
-__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                          uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ void produce_pass_mma(const PersistentArgs &args, int it, char *smem, MPipe &pp,
-                                 volatile int *s_abort)
-{
-    using C = MCfg;
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        int u = 0;
-        if (lane == 0) u = atomicAdd(args.work + (it & 1), 1);
-        u = __shfl_sync(0xFFFFFFFFu, u, 0);
-        const unsigned b = pp.ub & 1u, buse = pp.ub >> 1;
-        int pi = -1;
-        long long s = 0;
-        if (u < args.total_units) {
-            pi = find_problem(args.unit_start, args.n_prob, u);
-            s = args.probs[pi].ctr[0] + it;
-            if (s >= args.probs[pi].ctr[1]) continue;  // problem already at its pass end
-        }
-        if (buse >= 1 && !warp_wait(&pp.sempty[b], (buse - 1) & 1u, s_abort)) return;
-        UnitHdr *hdr = reinterpret_cast<UnitHdr *>(smem + C::OFF_HDR) + b;
-        SlotM *slots = reinterpret_cast<SlotM *>(smem + C::OFF_SLOTS) + b * C::MAXSLOT;
-        if (pi < 0) {
-            if (lane == 0) {
-                hdr->nslot = -1;
-                mbar_arrive(&pp.sfull[b]);
-            }
-            ++pp.ub;
-            return;
-        }
-        const Problem &pb = args.probs[pi];
-        const int tsplit = args.tsplit;
-        const int lu = u - __ldg(args.unit_start + pi);
-        const int nbx = (pb.W + 7) / 8;
-        const int tpart = lu % tsplit, blk = lu / tsplit;
-        const int x0 = (blk % nbx) * 8, y0 = (blk / nbx) * 8;
-        const int nchunks = pb.row_bytes / kChunk;
-        const int c0 = (int)((long long)nchunks * tpart / tsplit);
-        const int c1 = (int)((long long)nchunks * (tpart + 1) / tsplit);
-        const uint32_t sw = (uint32_t)s;
-        const uint32_t xs = pass_xor(pb, sw);
-        const int twoM = 2 * pb.M;
-        int nslot = 0;
-        for (int base = 0; base < 64; base += 32) {
-            const int lp = base + lane;
-            const int x = x0 + (lp & 7), y = y0 + (lp >> 3);
-            bool hit = false;
-            SlotM sl;
-            if (x < pb.W && y < pb.H) {
-                const int p = y * pb.W + x;
-                const int i = __ldg(pb.perm_inv + ((uint32_t)p ^ xs));
-                if (i < twoM) {
-                    const int partner = (int)((uint32_t)__ldg(pb.perm + (i ^ 1)) ^ xs);
-                    if (partner < pb.P) {
-                        hit = true;
-                        sl.wx = (lp & 7) + 8;
-                        sl.wy = (lp >> 3) + kR;
-                        sl.j = i >> 1;
-                        sl.side = i & 1;
-                        sl.p = p;
-                        sl.partner = partner;
-                        const int ox = wrapi(partner % pb.W - x, pb.W);
-                        const int oy = wrapi(partner / pb.W - y, pb.H);
-                        const int dx = 2 * ox <= pb.W ? ox : ox - pb.W;
-                        const int dy = 2 * oy <= pb.H ? oy : oy - pb.H;
-                        const bool near = dx * dx + dy * dy <= kR * kR;
-                        sl.pdx = near ? dx : 99;
-                        sl.pdy = near ? dy : 99;
-                    }
-                }
-            }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, hit);
-            if (hit) slots[nslot + __popc(m & ((1u << lane) - 1u))] = sl;
-            nslot += __popc(m);
-        }
-        if (lane == 0) {
-            hdr->nslot = nslot;
-            hdr->pi = pi;
-            hdr->tpart = tpart;
-            hdr->c0 = c0;
-            hdr->c1 = c1;
-            hdr->sw = sw;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&pp.sfull[b]);
-        ++pp.ub;
-        // tensor maps of this problem: boxes of 8 pixels x 20, 14 and 6 rows of one chunk
-        const char *tmap = args.tmaps + (size_t)pi * kMMaps * kTensorMapBytes;
-        // window rows y0-6 .. y0+13, split where they wrap (only the first and last block rows)
-        const bool top = y0 - kR < 0, bottom = y0 + kMWinH - kR > pb.H;
-        for (int base = 0; base < nslot; base += kMRound) {
-            for (int c = c0; c < c1; ++c) {
-                const unsigned g = pp.g, st = g % kMStages, use = g / kMStages;
-                if (use >= 1 && !warp_wait(&pp.empty[st], (use - 1) & 1u, s_abort)) return;
-                if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? *s_abort : 0, 0)) return;
-                char *dst = smem + st * C::STAGE;
-                if (lane == 0) mbar_arrive_expect_tx(&pp.full[st], (uint32_t)C::STAGE);
-                __syncwarp();
-                if (lane < 3) {
-                    const int bx = lane;
-                    const int tx = wrapi(x0 - 8 + 8 * bx, pb.W);  // a multiple of 8
-                    char *col = dst + mwin_off(8 * bx, 0);
-                    if (!top && !bottom) {
-                        tma_load_4d(col, tmap, 0, tx, y0 - kR, c, &pp.full[st]);
-                    } else if (top) {  // rows H-6 .. H-1, then 0 .. 13
-                        tma_load_4d(col, tmap + 2 * kTensorMapBytes, 0, tx, pb.H - kR, c,
-                                    &pp.full[st]);
-                        tma_load_4d(col + kR * 8 * kChunk, tmap + kTensorMapBytes, 0, tx, 0, c,
-                                    &pp.full[st]);
-                    } else {           // rows H-14 .. H-1, then 0 .. 5
-                        tma_load_4d(col, tmap + kTensorMapBytes, 0, tx, pb.H - (kMWinH - kR), c,
-                                    &pp.full[st]);
-                        tma_load_4d(col + (kMWinH - kR) * 8 * kChunk, tmap + 2 * kTensorMapBytes,
-                                    0, tx, 0, c, &pp.full[st]);
-                    }
-                }
-                pp.issued = g + 1;
-                ++pp.g;
-            }
-        }
-    }
-}
-
-__device__ void consume_pass_mma(const PersistentArgs &args, char *smem, MPipe &pp,
-                                 volatile int *s_abort)
-{
-    using C = MCfg;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gq = lane >> 2, jq = lane & 3;  // fragment row / column group
-    const uint32_t kBias0 = 0x64006400u;       // (1024, 1024)
-    const uint32_t kBias128 = 0x64806480u;     // (1152, 1152)
-    for (;;) {
-        const unsigned b = pp.ub & 1u, buse = pp.ub >> 1;
-        if (!warp_wait(&pp.sfull[b], buse & 1u, s_abort)) return;
-        const UnitHdr hdr = reinterpret_cast<const UnitHdr *>(smem + C::OFF_HDR)[b];
-        const SlotM *slots = reinterpret_cast<const SlotM *>(smem + C::OFF_SLOTS) + b * C::MAXSLOT;
-        if (hdr.nslot < 0) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&pp.sempty[b]);
-            ++pp.ub;
-            return;
-        }
-        const Problem &pb = args.probs[hdr.pi];
-        const int parts = 2 * args.tsplit;
-        for (int base = 0; base < hdr.nslot; base += kMRound) {
-            const int nround = min(kMRound, hdr.nslot - base);
-            const int mt_n = (nround + 15) >> 4;
-            // proposed pixels whose delta this warp stages: base + warp + 15 k
-            uint32_t kq_next[3];
-            const uint32_t *prow[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int sl = warp + kMNcw * k;
-                prow[k] = nullptr;
-                kq_next[k] = 0u;
-                if (sl < nround) {
-                    prow[k] = reinterpret_cast<const uint32_t *>(
-                                  chunk_ptr(pb, slots[base + sl].partner, 0)) + lane;
-                    kq_next[k] = __ldcg(prow[k] + (size_t)hdr.c0 * pb.P * kChunkWords);
-                }
-            }
-            float d[2][kMTilesPerWarp][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < kMTilesPerWarp; ++nt)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) d[mt][nt][e] = 0.f;
-            for (int c = hdr.c0; c < hdr.c1; ++c) {
-                const unsigned g = pp.g, st = g % kMStages, use = g / kMStages;
-                if (!warp_wait(&pp.full[st], use & 1u, s_abort)) return;
-                const char *win = smem + st * C::STAGE;
-                char *dbuf = smem + C::OFF_DELTA + st * (kMRound * kMDRow);
-                // stage the deltas of this warp's proposed pixels: partner chunk minus own chunk
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int sl = warp + kMNcw * k;
-                    if (sl < nround) {
-                        const SlotM &sm = slots[base + sl];
-                        const uint32_t kq = kq_next[k];
-                        if (c + 1 < hdr.c1)
-                            kq_next[k] = __ldcg(prow[k] + (size_t)(c + 1) * pb.P * kChunkWords);
-                        const uint32_t kp = *reinterpret_cast<const uint32_t *>(
-                            win + mwin_off(sm.wx, sm.wy) +
-                            ((((lane >> 2) ^ (sm.wx & 7)) << 4) | ((lane & 3) << 2)));
-                        *reinterpret_cast<uint32_t *>(dbuf + sl * kMDRow + lane * 4) =
-                            __vsub4(kq, kp);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&pp.dfull[st]);
-                if (!warp_wait(&pp.dfull[st], use & 1u, s_abort)) return;
-#pragma unroll 2
-                for (int ks = 0; ks < kChunk / 16; ++ks) {
-                    uint32_t a[2][4];
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        if (mt < mt_n) {
-                            const uint32_t x0 = *reinterpret_cast<const uint32_t *>(
-                                dbuf + (16 * mt + gq) * kMDRow + (4 * ks + jq) * 4);
-                            const uint32_t x1 = *reinterpret_cast<const uint32_t *>(
-                                dbuf + (16 * mt + gq + 8) * kMDRow + (4 * ks + jq) * 4);
-                            bytes_to_h2(x0 ^ 0x80808080u, kBias128, a[mt][0], a[mt][2]);
-                            bytes_to_h2(x1 ^ 0x80808080u, kBias128, a[mt][1], a[mt][3]);
-                        }
-                    }
-#pragma unroll
-                    for (int nt = 0; nt < kMTilesPerWarp; ++nt) {
-                        const int tile = warp * kMTilesPerWarp + nt;
-                        const int wy = tile / 3, wxb = 8 * (tile - 3 * (tile / 3));
-                        const uint32_t y = *reinterpret_cast<const uint32_t *>(
-                            win + mwin_off(wxb + gq, wy) + (((ks ^ gq) << 4) | (jq << 2)));
-                        uint32_t b0, b1;
-                        bytes_to_h2(y, kBias0, b0, b1);
-                        mma_16816(d[0][nt], a[0], b0, b1);
-                        if (mt_n > 1) mma_16816(d[1][nt], a[1], b0, b1);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&pp.empty[st]);
-                ++pp.g;
-            }
-            // epilogue: stencil entries of D into the class sums of the round's proposed pixels
-            const unsigned rbuf = pp.rb & 1u, ruse = pp.rb >> 1;
-            int *csum = reinterpret_cast<int *>(smem + C::OFF_CSUM) + rbuf * (kMRound * kMCsum);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                if (mt >= mt_n) continue;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int row = 16 * mt + gq + 8 * h;
-                    if (row >= nround) continue;
-                    const SlotM &sm = slots[base + row];
-#pragma unroll
-                    for (int nt = 0; nt < kMTilesPerWarp; ++nt) {
-                        const int tile = warp * kMTilesPerWarp + nt;
-                        const int wy = tile / 3, wxb = 8 * (tile - 3 * (tile / 3));
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int dx = wxb + 2 * jq + e - sm.wx, dy = wy - sm.wy;
-                            const int d2 = dx * dx + dy * dy;
-                            if (d2 < 1 || d2 > kR * kR || (dx == sm.pdx && dy == sm.pdy))
-                                continue;
-                            const int cl = c_cls_of_d2[d2];
-                            const int v = __float2int_rn(d[mt][nt][2 * h + e]);
-                            if (cl >= 0 && v != 0) atomicAdd(csum + row * kMCsum + cl, v);
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&pp.epi[rbuf]);
-            if (!warp_wait(&pp.epi[rbuf], ruse & 1u, s_abort)) return;
-            // the warp that staged a proposed pixel's deltas stores its class sums
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int sl = warp + kMNcw * k;
-                if (sl < nround && lane < kNCls) {
-                    const SlotM &sm = slots[base + sl];
-                    pb.side_cls[((size_t)sm.j * parts + sm.side * args.tsplit + hdr.tpart) *
-                                    kMaxClasses + lane] = csum[sl * kMCsum + lane];
-                    csum[sl * kMCsum + lane] = 0;
-                }
-            }
-            ++pp.rb;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&pp.sempty[b]);
-        ++pp.ub;
-    }
-}
-
-// phase 3 for one improving couple (one warp): keep it unless an interacting improving couple
-// has a higher priority, then swap; returns true (on every lane) when the swap was applied
 __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw, uint8_t flags)
 {
     const int lane = threadIdx.x & 31;
@@ -955,62 +588,33 @@ __device__ bool resolve_commit(const Problem &pb, int j, uint32_t sw, uint8_t fl
     return true;
 }
 
-template <int BX, int BY, int NCW, int SPW, int CB, int MINB, bool MMA>
+template <int BX, int BY, int NCW, int SPW, int CB, int MINB>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentArgs args)
 {
     using C = Cfg<BX, BY, NCW, SPW>;
-    static_assert(!MMA || (BX == 8 && BY == 8 && NCW == kMNcw && CB == 1),
-                  "the tensor-core variant is instantiated for 8 x 8 blocks, 8-bit counts");
     extern __shared__ __align__(128) char smem_raw[];
     __shared__ int s_err;
     __shared__ int s_abort;
-    // the tensor-core variant's stages start on a 1024-byte boundary (the swizzle atom)
     char *smem = smem_raw;
-    if constexpr (MMA) smem += (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
     const int nblocks = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (C::NT / 32) + warp, nwarps = nblocks * (C::NT / 32);
 
     Pipe pp;
-    MPipe mp;
-    if constexpr (MMA) {
-        mp.full = reinterpret_cast<uint64_t *>(smem + MCfg::OFF_BAR);
-        mp.empty = mp.full + kMStages;
-        mp.dfull = mp.full + 2 * kMStages;
-        mp.sfull = mp.full + 3 * kMStages;
-        mp.sempty = mp.sfull + 2;
-        mp.epi = mp.sfull + 4;
-        mp.g = mp.ub = mp.rb = mp.issued = 0;
-        int *csum = reinterpret_cast<int *>(smem + MCfg::OFF_CSUM);
-        for (int i = threadIdx.x; i < 2 * kMRound * kMCsum; i += C::NT) csum[i] = 0;
-    } else {
-        pp.full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
-        pp.empty = pp.full + 2;
-        pp.sfull = pp.full + 4;
-        pp.sempty = pp.full + 6;
-        pp.g = 0;
-        pp.ub = 0;
-        pp.issued = 0;
-    }
+    pp.full = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    pp.empty = pp.full + 2;
+    pp.sfull = pp.full + 4;
+    pp.sempty = pp.full + 6;
+    pp.g = 0;
+    pp.ub = 0;
+    pp.issued = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
-            if constexpr (MMA) {
-                mbar_init(&mp.sfull[i], 1);
-                mbar_init(&mp.sempty[i], NCW);
-                mbar_init(&mp.epi[i], NCW);
-            } else {
-                mbar_init(&pp.full[i], 1);
-                mbar_init(&pp.empty[i], NCW);
-                mbar_init(&pp.sfull[i], 1);
-                mbar_init(&pp.sempty[i], NCW);
-            }
+            mbar_init(&pp.full[i], 1);
+            mbar_init(&pp.empty[i], NCW);
+            mbar_init(&pp.sfull[i], 1);
+            mbar_init(&pp.sempty[i], NCW);
         }
-        if constexpr (MMA)
-            for (unsigned i = 0; i < kMStages; ++i) {
-                mbar_init(&mp.full[i], 1);
-                mbar_init(&mp.empty[i], NCW);
-                mbar_init(&mp.dfull[i], NCW);
-            }
         mbar_init_fence();
         s_abort = 0;
         s_err = 0;
@@ -1019,17 +623,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
 
     for (int it = 0; it < args.n_iter; ++it) {
         // ---- phase 1: evaluate (units from an atomic counter) -------------------------------
-        if constexpr (MMA) {
-            if (warp == NCW)
-                produce_pass_mma(args, it, smem, mp, &s_abort);
-            else
-                consume_pass_mma(args, smem, mp, &s_abort);
-        } else {
-            if (warp == NCW)
-                produce_pass<BX, BY, NCW, SPW>(args, it, smem, pp, &s_abort);
-            else
-                consume_pass<BX, BY, NCW, SPW, CB>(args, smem, pp, &s_abort);
-        }
+        if (warp == NCW)
+            produce_pass<BX, BY, NCW, SPW>(args, it, smem, pp, &s_abort);
+        else
+            consume_pass<BX, BY, NCW, SPW, CB>(args, smem, pp, &s_abort);
         __syncthreads();
         if (s_abort) {
             if (threadIdx.x == 0) atomicExch(&args.bar->error, 2u);
@@ -1101,11 +698,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) k_persistent(PersistentA
     if (s_abort || s_err) {
         // let this CTA's own copies land before it leaves (bounded)
         if (warp == NCW && lane == 0) {
-            const unsigned issued = MMA ? mp.issued : pp.issued;
-            const unsigned nst = MMA ? kMStages : 2u;
-            uint64_t *full = MMA ? mp.full : pp.full;
-            for (unsigned g = (issued >= nst ? issued - nst : 0); g < issued; ++g)
-                mbar_wait(&full[g % nst], (g / nst) & 1u);
+            const unsigned issued = pp.issued;
+            for (unsigned g = (issued >= 2u ? issued - 2u : 0); g < issued; ++g)
+                mbar_wait(&pp.full[g % 2u], (g / 2u) & 1u);
         }
         __syncthreads();
         return;
@@ -1171,12 +766,12 @@ __global__ void k_selftest_wait(int which, long long budget, GridBarrier *gb, in
     if (threadIdx.x == 0 && blockIdx.x == 0) result[0] = ok ? 0 : 1;
 }
 
-template <int BX, int BY, int NCW, int SPW, int CB, int MINB, bool MMA = false>
+template <int BX, int BY, int NCW, int SPW, int CB, int MINB>
 cudaError_t launch_cfg(const PersistentArgs &a0, int sms, cudaStream_t st)
 {
     using C = Cfg<BX, BY, NCW, SPW>;
-    constexpr size_t smem_bytes = MMA ? MCfg::SMEM : C::SMEM;
-    auto kern = k_persistent<BX, BY, NCW, SPW, CB, MINB, MMA>;
+    constexpr size_t smem_bytes = C::SMEM;
+    auto kern = k_persistent<BX, BY, NCW, SPW, CB, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
     if (e != cudaSuccess) return e;
@@ -1208,61 +803,10 @@ bool persistent_supported(const Problem &h)
            h.n_off == kNOff;
 }
 
-bool persistent_shape_is_mma(const PersistentShape &s)
-{
-    return s.bx == 8 && s.by == 8 && s.threads == (kMNcw + 1) * 32;
-}
-
 bool persistent_shape_fits(const Problem &h, const PersistentShape &s)
 {
-    // a window row must wrap at most once; the tensor-core variant reads 8-pixel boxes aligned
-    // to x = 0 mod 8 (16-bit counts run the IDP4A variant of the same shape)
-    if (persistent_shape_is_mma(s) && h.count_bytes == 1)
-        return persistent_supported(h) && h.W % 8 == 0 && h.W >= kMWinW && h.H % 8 == 0 &&
-               h.H >= kMWinW;
+    // a window row must wrap at most once
     return persistent_supported(h) && h.W >= s.bx + 2 * kR;
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-cudaError_t encode_count_tensor_maps(const Problem &h, void *out)
-{
-    // looked up once per process (thread-safe static initialisation)
-    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
-        void *ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
-                                             cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nullptr;
-        return reinterpret_cast<EncodeTiledFn>(ptr);
-    }();
-    if (!fn) {
-        cudaGetLastError();
-        return cudaErrorNotSupported;
-    }
-    // count planes [chunk][y][x][128 bytes]; a box is 8 pixels of 20, 14 or 6 rows, one chunk
-    const cuuint64_t dims[4] = {(cuuint64_t)kChunk, (cuuint64_t)h.W, (cuuint64_t)h.H,
-                                (cuuint64_t)(h.row_bytes / kChunk)};
-    const cuuint64_t strides[3] = {(cuuint64_t)kChunk, (cuuint64_t)h.W * kChunk,
-                                   (cuuint64_t)h.P * kChunk};
-    const cuuint32_t rows[kMMaps] = {(cuuint32_t)kMWinH, (cuuint32_t)(kMWinH - kR),
-                                     (cuuint32_t)kR};
-    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    for (int m = 0; m < kMMaps; ++m) {
-        const cuuint32_t box[4] = {(cuuint32_t)kChunk, 8u, rows[m], 1u};
-        const CUresult r =
-            fn(reinterpret_cast<CUtensorMap *>(static_cast<char *>(out) + m * kTensorMapBytes),
-               CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, (void *)h.counts, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
-    return cudaSuccess;
 }
 
 cudaError_t launch_fold_error(const GridBarrier *gb, const Problem *probs, int n_prob,
@@ -1285,12 +829,6 @@ cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &sh
                               int sms, cudaStream_t st)
 {
     cudaError_t e = cudaErrorInvalidValue;
-    if (persistent_shape_is_mma(shape) && cb == 1) {
-        if (!a.tmaps) return cudaErrorInvalidValue;
-        e = launch_cfg<8, 8, kMNcw, 4, 1, 1, true>(a, sms, st);
-        note_launches(1);
-        return e;
-    }
 #define BN_SHAPE(BX, BY, NCW, KMAX, MINB)                                                     \
     if (shape.bx == BX && shape.by == BY && shape.threads == (NCW + 1) * 32 &&                \
         shape.spw == KMAX)                                                                     \

@@ -28,13 +28,7 @@ struct PersistentArgs {
     int n_iter;             // passes in this launch (problems stop at their own pass end)
     GridBarrier *bar;
     int *work;              // [2] unit counters of phase 1, by pass parity; zeroed per launch
-    const char *tmaps;      // [n_prob][3] TMA tensor maps of the count planes, or null; used
-                            // by the tensor-core variant
 };
-
-// Bytes of one TMA tensor map (CUtensorMap); the tensor-core variant keeps three per problem
-constexpr int kTensorMapBytes = 128;
-constexpr int kTensorMapsPerProblem = 3;
 
 // CTA shape: block of bx x by pixels, threads per CTA, proposed pixels per warp per round
 struct PersistentShape {
@@ -43,22 +37,14 @@ struct PersistentShape {
 
 // Instantiated CTA shapes: X(bx, by, compute warps, proposed pixels per warp per round, min
 // CTAs per SM); every CTA has one more warp, the producer (threads = 32 * (compute warps + 1)).
-// The 8 x 8 shape with 15 compute warps runs the tensor-core variant for 8-bit counts on tiles
-// whose sides are multiples of 8 (at least 24), and the IDP4A variant otherwise.
 #define BN_PERSISTENT_SHAPES(X) \
     X(8, 8, 7, 4, 2)            \
     X(16, 8, 15, 4, 1)          \
-    X(8, 16, 15, 4, 1)          \
-    X(8, 8, 15, 4, 1)
+    X(8, 16, 15, 4, 1)
 
 int persistent_units_per_problem(const Problem &h, int bx, int by, int tsplit);
 bool persistent_supported(const Problem &h);
 bool persistent_shape_fits(const Problem &h, const PersistentShape &s);
-// the shape runs the tensor-core variant on 8-bit counts
-bool persistent_shape_is_mma(const PersistentShape &s);
-// encode the TMA tensor maps of a problem's count planes into out (host;
-// kTensorMapsPerProblem x kTensorMapBytes bytes)
-cudaError_t encode_count_tensor_maps(const Problem &h, void *out);
 cudaError_t launch_persistent(const PersistentArgs &a, const PersistentShape &shape, int cb,
                               int sms, cudaStream_t st);
 cudaError_t launch_fold_error(const GridBarrier *gb, const Problem *probs, int n_prob,

@@ -5,8 +5,12 @@
 //   1. admits queued requests while a slot is free and the device-memory budget allows; each
 //      admitted request gets a sampler initialised on a side stream (shifts, integrands,
 //      permutation, counts), so admission overlaps the chunk already running on the GPU;
-//   2. when the set of resident requests changed, rebuilds the fused batch over them (one
-//      launch sequence for all their pairs, uneven tiles included);
+//   2. when the set of resident requests changed, rebuilds the fused batches over them: one for
+//      the requests that run on the tensor-core schedule, one for the rest (one launch sequence
+//      per batch for all its pairs, uneven tiles included).  Which batch a request joins is
+//      the autotuner's choice for its signature (count width, N, T, radius, pair count and the
+//      tile sides rounded up to powers of two), timed once on the first request of that
+//      signature, on a scratch copy of its state, and cached for the server's lifetime;
 //   3. runs up to sweeps_per_chunk passes for every resident request, each stopping at its own
 //      remaining budget inside the launch;
 //   4. retires the requests whose budget is spent (final Eq. 1, optimised shifts to host,
@@ -46,7 +50,26 @@ struct Resident {
     double t_submit, t_admit;
     int64_t bytes;
     bool cancel;
+    bool tensor;  // member of the tensor-core batch
 };
+
+// passes of each candidate schedule when a signature is tuned
+constexpr int kTuneSweeps = 8;
+
+int ceil_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+std::string signature(const bn_config &c)
+{
+    return std::to_string(c.n_points > 256 ? 2 : 1) + "/" + std::to_string(c.n_points) + "/" +
+           std::to_string(c.n_integrands) + "/" + std::to_string(c.radius) + "/" +
+           std::to_string(c.n_pairs) + "/" + std::to_string(ceil_pow2(c.width)) + "x" +
+           std::to_string(ceil_pow2(c.height));
+}
 
 }  // namespace
 
@@ -69,7 +92,8 @@ struct bn_server {
     int64_t mem_used = 0;
     bn_server_stats st{};
     Clock::time_point t0;
-    bn_batch *batch = nullptr;
+    bn_batch *batch[2] = {nullptr, nullptr};  // [0] other schedules, [1] tensor-core schedule
+    std::map<std::string, bool> tuned;         // signature -> runs on the tensor-core schedule
     bool dirty = true;
     std::string thread_error;
 
@@ -140,7 +164,7 @@ void loop(bn_server *sv)
         for (const auto &p : admit) {
             bn::TraceRange trace_("bn.server.admit");
             Resident r{p.id, p.req, nullptr, p.req.n_sweeps, p.t_submit, 0.0,
-                       bn::estimate_device_bytes(p.req.cfg), false};
+                       bn::estimate_device_bytes(p.req.cfg), false, false};
             const int rc = bn_sampler_init(&p.req.cfg, sv->init, &r.s);
             r.t_admit = sv->now();
             if (rc != BN_OK) {
@@ -175,14 +199,39 @@ void loop(bn_server *sv)
             sv->st.memory_in_use = sv->mem_used;
         }
         if (sv->active.empty()) continue;
-        // ---- 2. fused batch over the resident requests ----------------------------------------
+        // ---- 2. fused batches over the resident requests --------------------------------------
         if (sv->dirty) {
-            if (sv->batch) bn_batch_destroy(sv->batch);
-            sv->batch = nullptr;
-            std::vector<bn_sampler *> members;
-            for (auto &r : sv->active) members.push_back(r.s);
-            if (bn_batch_create(members.data(), (int32_t)members.size(), sv->run, &sv->batch) !=
-                BN_OK) {
+            bool ok = true;
+            for (auto &r : sv->active) {
+                if (!ok) break;
+                const std::string key = signature(r.req.cfg);
+                auto it = sv->tuned.find(key);
+                if (it == sv->tuned.end()) {
+                    bool tc = sv->cfg.tensor_policy == BN_SERVE_TENSOR_ALWAYS;
+                    if (sv->cfg.tensor_policy == BN_SERVE_TENSOR_TUNED && bn::tensor_capable(r.s)) {
+                        bn::TraceRange trace_("bn.server.tune");
+                        bn_schedule best{};
+                        ok = bn::tune_schedule(r.s, kTuneSweeps, &best) == BN_OK;
+                        tc = ok && best.kind == BN_SCHEDULE_TENSOR;
+                        std::lock_guard<std::mutex> lk(sv->mu);
+                        ++sv->st.tunes;
+                    }
+                    it = sv->tuned.emplace(key, tc).first;
+                }
+                r.tensor = it->second && bn::tensor_capable(r.s);
+            }
+            for (int g = 0; g < 2 && ok; ++g) {
+                if (sv->batch[g]) bn_batch_destroy(sv->batch[g]);
+                sv->batch[g] = nullptr;
+                std::vector<bn_sampler *> members;
+                for (auto &r : sv->active)
+                    if (r.tensor == (g == 1)) members.push_back(r.s);
+                if (members.empty()) continue;
+                ok = bn::batch_create_as(members.data(), (int32_t)members.size(), sv->run,
+                                         g ? BN_SCHEDULE_TENSOR : BN_SCHEDULE_AUTO,
+                                         &sv->batch[g]) == BN_OK;
+            }
+            if (!ok) {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 sv->thread_error = bn_last_error();
                 break;
@@ -191,16 +240,21 @@ void loop(bn_server *sv)
         }
         // ---- 3. one chunk of passes -------------------------------------------------------------
         std::vector<int32_t> n(sv->active.size());
+        std::vector<int32_t> ng[2];
         int64_t props = 0;
         for (size_t i = 0; i < sv->active.size(); ++i) {
             n[i] = std::min(sv->active[i].left, sv->cfg.sweeps_per_chunk);
+            ng[sv->active[i].tensor ? 1 : 0].push_back(n[i]);  // member order of the batches
             bn_info info;
             bn_get_info(sv->active[i].s, &info);
             props += (int64_t)n[i] * info.couples * sv->active[i].req.cfg.n_pairs;
         }
         bn::TraceRange trace_chunk("bn.server.chunk");
-        if (bn_batch_optimize_each(sv->batch, n.data(), nullptr) != BN_OK ||
-            cudaStreamSynchronize(sv->run) != cudaSuccess) {
+        bool run_ok = true;
+        for (int g = 1; g >= 0 && run_ok; --g)
+            if (!ng[g].empty())
+                run_ok = bn_batch_optimize_each(sv->batch[g], ng[g].data(), nullptr) == BN_OK;
+        if (!run_ok || cudaStreamSynchronize(sv->run) != cudaSuccess) {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->thread_error = bn_last_error();
             break;
@@ -230,13 +284,16 @@ void loop(bn_server *sv)
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->active.swap(keep);
         ++sv->st.chunks;
+        if (!ng[1].empty()) ++sv->st.tensor_chunks;
         sv->st.proposals += props;
         sv->st.active = (int64_t)sv->active.size();
         sv->st.memory_in_use = sv->mem_used;
     }
     // shutdown: free whatever is still resident
-    if (sv->batch) bn_batch_destroy(sv->batch);
-    sv->batch = nullptr;
+    for (auto &b : sv->batch) {
+        if (b) bn_batch_destroy(b);
+        b = nullptr;
+    }
     for (auto &r : sv->active) bn_sampler_destroy(r.s);
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->active.clear();
@@ -263,6 +320,8 @@ int bn_server_create(const bn_server_config *cfg, bn_server **out)
     if (cfg->sweeps_per_chunk < 1 || cfg->sweeps_per_chunk > 500)
         return sfail(BN_ERR_INVALID_ARG, "sweeps_per_chunk must be in [1, 500]");
     if (cfg->memory_budget_bytes < 0) return sfail(BN_ERR_INVALID_ARG, "negative memory budget");
+    if (cfg->tensor_policy < BN_SERVE_TENSOR_TUNED || cfg->tensor_policy > BN_SERVE_TENSOR_NEVER)
+        return sfail(BN_ERR_INVALID_ARG, "tensor_policy must be a BN_SERVE_TENSOR_* value");
     auto *sv = new bn_server();
     sv->cfg = *cfg;
     sv->device = cfg->device;

@@ -12,10 +12,14 @@
 // in tensor memory; about a fifth of the entries lie inside the radius and are kept.
 //
 // Exactness.  The A operand holds the centred counts c_q = k_q - N/2 (|c| <= N/2), the B operand
-// the deltas (|delta| <= N), both exact in f16; every entry of D is an integer of magnitude at
-// most T (N/2) N <= 2^24 (checked at plan time), exact in the f32 accumulators.  The centring
-// adds (N/2) (sum_t delta_n[t]) x |S_c(n)| to S_c(n); side b carries -delta_a and on a torus
-// |S_c(a) \ b| = |S_c(b) \ a|, so the two corrections cancel in A_c.
+// the deltas (|delta| <= N), both exact in f16.  The integrands of a product are summed in
+// accumulator rounds of R stages of 64, R 64 N^2 <= 2^25: every partial sum of a round is an
+// integer of magnitude at most R 64 (N/2) N <= 2^24, exact in the f32 accumulators, and the
+// rounds add as integers (one round when T N^2 <= 2^25).  The centring adds
+// (N/2) (sum_t delta_n[t]) x |S_c(n)| to S_c(n); side b carries -delta_a and on a torus
+// |S_c(a) \ b| = |S_c(b) \ a|, so the two corrections cancel in A_c, whose magnitude is at most
+// 2 x 12 x T (N/2) N = 12 T N^2 (at most 12 pixels share a squared distance within radius 8):
+// below 2^31 for T N^2 <= 2^27, the plan-time limit.
 //
 // A pass:
 //   k_tc_lists     one warp per couple: its class sums cleared, its f16 delta row k_b - k_a
@@ -37,7 +41,8 @@
 //                    3 MMA warps          stage g issued by warp g mod 3: four tcgen05.mma (A
 //                                         from tensor memory, B from shared memory, K = 16)
 //                                         into one of two accumulators (M = 128, N <= 160),
-//                                         which the epilogue zeroes as it reads them
+//                                         which the epilogue zeroes as it reads them; a
+//                                         product takes one accumulator per round
 //                    8 epilogue warps     16 accumulator columns per warp and step, transposed
 //                                         through shared memory 32 columns at a time; for
 //                                         radius 6 each warp owns whole distance classes and
@@ -282,8 +287,9 @@ struct TcUnit {
     const int4 *list;        // the patch's list of proposed pixels
     const uint16_t *delta;   // the problem's per-pass delta rows
     int32_t *side;           // the problem's class sums
-    int flags;               // kUnitTable: 2-D table path holds; kUnitStatic6: radius-6 path
-    int pad;
+    int flags;               // kUnitTable: 2-D table path holds; kUnitStatic6: radius-6 path;
+                             // accumulator rounds per product << 8
+    int kper;                // stages per accumulator round (exact f32 partial sums)
 };
 static_assert(sizeof(TcUnit) == 64, "unit table entry");
 constexpr int kUnitTable = 1, kUnitStatic6 = 2;
@@ -311,6 +317,12 @@ __device__ __forceinline__ int unit_count_bytes(const Unit &d) { return d.t->geo
 __device__ __forceinline__ int unit_stages(const Unit &d)
 {
     return unit_row_bytes(d) / (64 * unit_count_bytes(d));
+}
+// stages per accumulator round: the most R with R 64 N^2 <= 2^25, at most all of them
+__host__ __device__ __forceinline__ int tc_round_stages(int N, int stages)
+{
+    const long long r = (1ll << 25) / (64ll * N * N);
+    return r < 1 ? 1 : (r < stages ? (int)r : stages);
 }
 
 // 2-D class table of the epilogue's table path: offsets (dx, dy) from a proposed pixel to a
@@ -713,6 +725,7 @@ __device__ void tc_produce_b(const TcArgs &args, const TcUnit *utab, int nu, cha
 // which the warps' products accumulate does not matter; every product accumulates onto an
 // accumulator the epilogue has zeroed.  A product is complete when every MMA warp has committed
 // it (acc_full counts kMmaWarps arrivals).
+template <bool kRounds>
 __device__ void tc_mma(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
                        uint64_t *full, uint64_t *empty, uint64_t *acc_full, uint64_t *acc_empty,
                        uint64_t *done, uint32_t tmem, volatile int *abort_flag,
@@ -727,21 +740,23 @@ __device__ void tc_mma(const TcArgs &args, const TcUnit *utab, int nu, char *sme
         int pi;
         const Unit d = unit_at(utab, ku, pi);
         if (d.cnt <= 0) continue;
-        const int kst = unit_stages(d);
-        for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB) {
+        const int kst = unit_stages(d), kper = kRounds ? d.t->kper : kst;
+        for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB)
+        for (int s0 = 0; s0 < kst && ok; s0 += kper) {  // the product's accumulator rounds
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
+            const int sn = kst - s0 < kper ? kst - s0 : kper;
             const uint32_t buf = jb & 1u;
-            // this warp's stages of the product: g .. g + kst - 1 with g' mod kMmaWarps == mw
+            // this warp's stages of the round: g .. g + sn - 1 with g' mod kMmaWarps == mw
             const uint32_t first = g + (uint32_t)((mw - (int)(g % kMmaWarps) + kMmaWarps) % kMmaWarps);
-            if (first < g + (uint32_t)kst) {
+            if (first < g + (uint32_t)sn) {
                 ok = tc_wait_warp(&acc_empty[buf], ((jb >> 1) & 1u) ^ 1u, abort_flag);
                 if (!ok) break;
                 tc::fence_after_sync();
             }
             const uint32_t dt = tmem + buf * kAccCols;
             const uint32_t idesc = tc::idesc_f16_f32(kTcM, npad);
-            for (uint32_t gs = first; gs < g + (uint32_t)kst; gs += kMmaWarps) {
+            for (uint32_t gs = first; gs < g + (uint32_t)sn; gs += kMmaWarps) {
                 const uint32_t as = gs % kStages;
                 ok = tc_wait_warp(&full[as], (gs / kStages) & 1u, abort_flag);
                 if (!ok) break;
@@ -758,10 +773,10 @@ __device__ void tc_mma(const TcArgs &args, const TcUnit *utab, int nu, char *sme
                 issued = true;
             }
             if (!ok) break;
-            // this warp's part of the product is issued (possibly none of it)
+            // this warp's part of the round is issued (possibly none of it)
             if (lane == 0) tc::mma_commit(&acc_full[buf]);
             __syncwarp();
-            g += (uint32_t)kst;
+            g += (uint32_t)sn;
             ++jb;
         }
     }
@@ -776,6 +791,7 @@ __device__ void tc_mma(const TcArgs &args, const TcUnit *utab, int nu, char *sme
 // ---- epilogue warps ----------------------------------------------------------------------------
 // Warp w reads lane quadrant w mod 4 (patch pixels 32 (w mod 4) ..) and columns 16 (w / 4) ..
 // of every 32-column step.
+template <bool kRounds>
 __device__ void tc_epilogue(const TcArgs &args, const TcUnit *utab, int nu, char *smem,
                             uint64_t *acc_full, uint64_t *acc_empty, uint32_t tmem,
                             volatile int *abort_flag)
@@ -834,7 +850,9 @@ __device__ void tc_epilogue(const TcArgs &args, const TcUnit *utab, int nu, char
         const int lt = (ly - kPH / 2 + tab2_dy(r)) * tw + (lx - kPW / 2 + tab2_dx(r));
         int32_t *const side = d.t->side;
         const int4 *list = d.t->list;
-        for (int n0 = 0; n0 < d.cnt; n0 += kNB) {
+        for (int n0 = 0; n0 < d.cnt && ok; n0 += kNB)
+        for (int rr = 0; rr < (kRounds ? (d.t->flags >> 8) : 1); ++rr) {  // one accumulator per
+                                                                         // round, sums added
             const int nn = d.cnt - n0 < kNB ? d.cnt - n0 : kNB;
             const int npad = (nn + 15) & ~15;
             const uint32_t buf = jb & 1u;
@@ -951,6 +969,8 @@ __device__ void tc_epilogue(const TcArgs &args, const TcUnit *utab, int nu, char
     }
 }
 
+// kRounds: some problem of the launch sums its integrands in more than one accumulator round
+template <bool kRounds>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -992,8 +1012,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
         const bool fast = tab2_ok(pb.W, pb.H, pb.radius);
         const bool st6 = fast && pb.radius == 6 && pb.n_cls == kCls6 &&
                          classes_match6(pb.d2, std::make_integer_sequence<int, kCls6>{});
-        t.flags = (fast ? kUnitTable : 0) | (st6 ? kUnitStatic6 : 0);
-        t.pad = 0;
+        t.kper = tc_round_stages(pb.N, tc_stages(pb));
+        t.flags = (fast ? kUnitTable : 0) | (st6 ? kUnitStatic6 : 0) |
+                  (((tc_stages(pb) + t.kper - 1) / t.kper) << 8);
         utab[k] = t;
     }
     if (threadIdx.x == 0) {
@@ -1032,7 +1053,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
     __syncthreads();
     tc::fence_after_sync();
     if (warp < kConvWarp0)
-        tc_epilogue(args, utab, nu, smem, acc_full, acc_empty, tmem, s_abort);
+        tc_epilogue<kRounds>(args, utab, nu, smem, acc_full, acc_empty, tmem, s_abort);
     else if (warp < kProdWarp0)
         tc_convert(args, utab, nu, smem, a_full, a_empty, full, empty, tmem, s_abort);
     else if (warp < kLoadWarp)
@@ -1041,7 +1062,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_stencil(TcArgs args)
         if ((threadIdx.x & 31) == 0)
             tc_load_a(args, utab, nu, smem, a_full, a_empty, s_abort, s_zero);
     } else
-        tc_mma(args, utab, nu, smem, full, empty, acc_full, acc_empty, done, tmem, s_abort, s_zero);
+        tc_mma<kRounds>(args, utab, nu, smem, full, empty, acc_full, acc_empty, done, tmem, s_abort,
+                        s_zero);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -1265,15 +1287,17 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
 
 bool tc_supported(const Problem &h)
 {
-    // counts below 1024 (f16 read as 1024 + k), centred products exact in f32:
-    // T (N / 2) N <= 2^24
+    // counts below 1024 (f16 read as 1024 + k); accumulator rounds of at least one stage exact
+    // in f32 (64 N^2 <= 2^25, N <= 724) and class sums within int32 (12 T N^2 < 2^31)
     const bool counts_ok = h.count_bytes == 1 || (h.count_bytes == 2 && h.N <= 512);
-    const bool exact = (long long)h.T * h.N * h.N <= (1ll << 25);
+    const bool exact = (long long)h.T * h.N * h.N <= (1ll << 27);
     return counts_ok && exact && h.radius >= 1 && h.radius <= 8 && h.W >= 2 * h.radius + 1 &&
            h.H >= 2 * h.radius + 1 && h.n_cls <= kMaxClasses && h.row_bytes % 128 == 0;
 }
 
 int tc_units_per_problem(const Problem &h) { return h.tc_npx * h.tc_npy; }
+
+bool tc_rounds(const Problem &h) { return tc_round_stages(h.N, tc_stages(h)) < tc_stages(h); }
 
 size_t tc_delta_bytes(const Problem &h) { return (size_t)h.M * tc_stages(h) * 64 * 2; }
 
@@ -1310,8 +1334,12 @@ cudaError_t encode_tc_tensor_map(const Problem &h, void *out)
 
 cudaError_t prepare_tc()
 {
-    return cudaFuncSetAttribute(k_tc_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_stencil<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tc_stencil<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes);
+    return e;
 }
 
 cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm)
@@ -1331,7 +1359,10 @@ cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm
         for (int b0 = 0; b0 < tl.total_units; b0 += per * tl.sms) {
             const int cnt = tl.total_units - b0 < per * tl.sms ? tl.total_units - b0 : per * tl.sms;
             const TcArgs a{tl.dprob, tl.n_prob, tl.units, b0, cnt, per, tl.tmaps};
-            k_tc_stencil<<<(cnt + per - 1) / per, kTcThreads, kSmemBytes, st>>>(a);
+            if (tl.rounds)
+                k_tc_stencil<true><<<(cnt + per - 1) / per, kTcThreads, kSmemBytes, st>>>(a);
+            else
+                k_tc_stencil<false><<<(cnt + per - 1) / per, kTcThreads, kSmemBytes, st>>>(a);
             note_launches(1);
         }
         if (timed) tm->end(st);

@@ -290,8 +290,10 @@ class Server:
     background thread of the library, and retired with their final Eq. 1 and shifts."""
 
     def __init__(self, max_slots: int = 64, sweeps_per_chunk: int = 50,
-                 memory_budget_bytes: int = 0, device: int = 0):
-        self.cfg = L.BnServerConfig(device, max_slots, sweeps_per_chunk, 0, memory_budget_bytes)
+                 memory_budget_bytes: int = 0, device: int = 0,
+                 tensor_policy: int = L.BN_SERVE_TENSOR_TUNED):
+        self.cfg = L.BnServerConfig(device, max_slots, sweeps_per_chunk, tensor_policy,
+                                    memory_budget_bytes)
         self._h = ctypes.c_void_p()
         L.check(L.load().bn_server_create(ctypes.byref(self.cfg), ctypes.byref(self._h)))
 

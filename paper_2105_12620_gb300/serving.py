@@ -55,9 +55,21 @@ def offered_proposals(reqs: list[Request]) -> int:
     return sum(couples_per_pass(r.width, r.height) * r.n_pairs * r.n_sweeps for r in reqs)
 
 
+def latency_percentiles(lat, wait) -> dict:
+    """p50 / p99 of the per-request latencies (submit to done) and queueing delays (submit to
+    admit), numpy's linear interpolation between order statistics; None for no requests."""
+    lat, wait = np.asarray(lat, dtype=np.float64), np.asarray(wait, dtype=np.float64)
+    pct = (lambda a, q: float(np.percentile(a, q)) if len(a) else None)
+    return {"p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+            "mean_latency_s": float(lat.mean()) if len(lat) else None,
+            "p50_queue_s": pct(wait, 50), "p99_queue_s": pct(wait, 99)}
+
+
 def summarize(reqs: list[Request], results: dict, makespan_s: float, proposals: int,
               depth_samples: list[tuple[int, int]]) -> dict:
-    """Latency percentiles (submit to done, server clock), queueing delay, rates."""
+    """Latency percentiles (submit to done, server clock), queueing delay, rates; the raw
+    per-request latencies and delays ride along under "latencies_s" and "queue_s" so that
+    several streams can be pooled."""
     lat = np.array([results[i].t_done - results[i].t_submit for i in range(len(reqs))])
     wait = np.array([results[i].t_admit - results[i].t_submit for i in range(len(reqs))])
     ok = sum(1 for r in results.values() if r.status == 0)
@@ -66,11 +78,8 @@ def summarize(reqs: list[Request], results: dict, makespan_s: float, proposals: 
     active = np.array([a for _, a in depth_samples]) if depth_samples else np.zeros(1)
     return {
         "requests": len(reqs), "completed": ok,
-        "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
-        "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
-        "mean_latency_s": float(lat.mean()) if len(lat) else None,
-        "p50_queue_s": float(np.percentile(wait, 50)) if len(wait) else None,
-        "p99_queue_s": float(np.percentile(wait, 99)) if len(wait) else None,
+        **latency_percentiles(lat, wait),
+        "latencies_s": [float(v) for v in lat], "queue_s": [float(v) for v in wait],
         "offered_req_per_s": len(reqs) / span_arrivals if span_arrivals > 0 else None,
         "served_req_per_s": ok / makespan_s if makespan_s > 0 else None,
         "proposals_per_s": proposals / makespan_s if makespan_s > 0 else None,

@@ -93,10 +93,11 @@ int main(void) {
     S(bn_sweep_stats) S(bn_info) O(bn_info, sweep)
     S(bn_kernel_time) O(bn_kernel_time, launches)
     S(bn_schedule) O(bn_schedule, tsplit)
-    S(bn_server_config) O(bn_server_config, memory_budget_bytes)
+    S(bn_server_config) O(bn_server_config, tensor_policy) O(bn_server_config, memory_budget_bytes)
     S(bn_request) O(bn_request, n_sweeps) O(bn_request, user_tag)
     S(bn_result) O(bn_result, status) O(bn_result, energy) O(bn_result, t_done)
-    S(bn_server_stats) O(bn_server_stats, memory_budget)
+    S(bn_server_stats) O(bn_server_stats, memory_budget) O(bn_server_stats, tensor_chunks)
+    O(bn_server_stats, tunes)
     return 0;
 }
 """
@@ -127,7 +128,7 @@ def test_binding_constants_match_the_header(tmp_path):
     """Every #define BN_* value of include/bn_sampler.h equals the binding's constant."""
     import re
     names = re.findall(r"^#define (BN_(?:OK|ERR_\w+|MODE_\w+|OBJECTIVE_\w+|SCHEDULE_\w+|"
-                       r"INTEGRANDS_\w+))\b", open(L.HEADER).read(), re.M)
+                       r"INTEGRANDS_\w+|SERVE_\w+))\b", open(L.HEADER).read(), re.M)
     assert "BN_SCHEDULE_TENSOR" in names
     src = tmp_path / "consts.c"
     src.write_text("#include <stdio.h>\n#include \"bn_sampler.h\"\nint main(void) {\n" +
@@ -148,9 +149,12 @@ def test_binding_constants_match_the_header(tmp_path):
     (dict(sweeps_per_chunk=0), "sweeps_per_chunk"),
     (dict(sweeps_per_chunk=501), "sweeps_per_chunk"),
     (dict(memory_budget_bytes=-1), "budget"),
+    (dict(tensor_policy=-1), "tensor_policy"),
+    (dict(tensor_policy=3), "tensor_policy"),
 ])
 def test_server_config_validated_on_the_host(lib, kw, needle):
-    base = dict(device=0, max_slots=4, sweeps_per_chunk=10, reserved=0, memory_budget_bytes=0)
+    base = dict(device=0, max_slots=4, sweeps_per_chunk=10, tensor_policy=0,
+                memory_budget_bytes=0)
     base.update(kw)
     h = ctypes.c_void_p()
     assert lib.bn_server_create(ctypes.byref(L.BnServerConfig(**base)),

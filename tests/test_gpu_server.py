@@ -30,14 +30,30 @@ MIX_PLAIN = [
 ]
 
 
+# tensor-core capable requests (sides >= 13, N <= 512) beside ones that are not: N = 1024
+# (counts of 1024 leave the f16 operand's exact range) and a 12 x 40 tile (narrower than the
+# stencil)
+MIX_TENSOR = [
+    (64, 48, 64, 1024, 1, 21, 31),
+    (37, 29, 16, 256, 2, 33, 32),
+    (96, 80, 256, 512, 1, 12, 33),
+    (20, 52, 128, 1000, 1, 17, 34),
+    (48, 44, 256, 1024, 2, 9, 35),    # two accumulator rounds
+]
+MIX_NOT_TENSOR = [
+    (40, 40, 1024, 16, 1, 14, 41),
+    (12, 40, 16, 64, 1, 19, 42),
+]
+
+
 def alone(w, h, n, t, pairs, passes, seed):
     with Sampler(w, h, n, t, seed=seed, n_pairs=pairs) as s:
         s.optimize(passes, stats=False)
         return np.asarray(s.energy()), s.shifts()
 
 
-def run_server(mix, max_slots, chunk, late=()):
-    with Server(max_slots=max_slots, sweeps_per_chunk=chunk) as sv:
+def run_server(mix, max_slots, chunk, late=(), policy=L.BN_SERVE_TENSOR_TUNED):
+    with Server(max_slots=max_slots, sweeps_per_chunk=chunk, tensor_policy=policy) as sv:
         ids = {}
         for k, (w, h, n, t, pairs, passes, seed) in enumerate(mix):
             ids[sv.submit(w, h, n, t, passes, seed=seed, n_pairs=pairs, user_tag=k)] = k
@@ -74,6 +90,38 @@ def test_each_result_equals_the_request_alone(mix, max_slots, chunk):
         np.testing.assert_array_equal(sh, sh_ref)
         np.testing.assert_array_equal(e, e_ref)
         assert r.t_submit <= r.t_admit <= r.t_done
+
+
+@pytest.mark.parametrize("policy", [L.BN_SERVE_TENSOR_ALWAYS, L.BN_SERVE_TENSOR_TUNED,
+                                    L.BN_SERVE_TENSOR_NEVER], ids=["always", "tuned", "never"])
+def test_tensor_batch_results_equal_the_request_alone(policy):
+    """Requests on the tensor-core batch, beside requests the schedule refuses, give the results
+    of the same requests run alone (on the default schedule)."""
+    mix = MIX_TENSOR + MIX_NOT_TENSOR
+    out, stats = run_server(mix, 4, 8, policy=policy)
+    assert stats["completed"] == len(mix) and stats["failed"] == 0
+    if policy == L.BN_SERVE_TENSOR_ALWAYS:
+        assert stats["tensor_chunks"] > 0 and stats["tunes"] == 0
+    if policy == L.BN_SERVE_TENSOR_NEVER:
+        assert stats["tensor_chunks"] == 0 and stats["tunes"] == 0
+    if policy == L.BN_SERVE_TENSOR_TUNED:
+        # one trial per signature of a capable request, none for the others
+        assert stats["tunes"] == len(MIX_TENSOR)
+    for k, cfg in enumerate(mix):
+        e_ref, sh_ref = alone(*cfg)
+        e, sh, _ = out[k]
+        np.testing.assert_array_equal(sh, sh_ref)
+        np.testing.assert_array_equal(e, e_ref)
+
+
+def test_tensor_batch_with_mid_flight_arrivals():
+    first, late = MIX_TENSOR[:2] + MIX_NOT_TENSOR[:1], MIX_TENSOR[2:] + MIX_NOT_TENSOR[1:]
+    out, stats = run_server(first, 8, 5, late=late, policy=L.BN_SERVE_TENSOR_ALWAYS)
+    assert stats["completed"] == len(first) + len(late) and stats["tensor_chunks"] > 0
+    for k, cfg in enumerate(first + late):
+        e_ref, sh_ref = alone(*cfg)
+        np.testing.assert_array_equal(out[k][1], sh_ref)
+        np.testing.assert_array_equal(out[k][0], e_ref)
 
 
 def test_requests_arriving_mid_flight_are_admitted_and_exact():

@@ -58,7 +58,11 @@ LOCKSTEP = [
     # 16-bit counts (N >= 128), centred f16 operands
     (32, 32, 256, 64, 1, 6, 3, 10),     # N = 256
     (45, 37, 128, 200, 2, 6, 4, 8),     # N = 128, two pairs, ragged patches and T
-    (40, 40, 256, 512, 1, 6, 9, 4),     # T N^2 = 2^25: the exactness bound of centred products
+    (40, 40, 256, 512, 1, 6, 9, 4),     # T N^2 = 2^25: the last size with one accumulator round
+    (36, 30, 256, 1024, 1, 6, 8, 4),    # two accumulator rounds of 8 stages (T N^2 = 2^26)
+    (30, 28, 256, 1300, 1, 6, 13, 3),   # three rounds (8, 8, 5 stages), near the T limit of N
+    (29, 27, 512, 320, 1, 6, 10, 3),    # N = 512: rounds of 2 stages (2, 2, 1)
+    (31, 33, 512, 300, 2, 3, 11, 4),    # ragged T over rounds of 2 stages, two pairs, radius 3
     (33, 29, 512, 100, 1, 3, 2, 6),     # N = 512 (counts up to 512), radius 3
     (29, 31, 128, 70, 1, 8, 6, 6),      # radius 8 with 16-bit counts
 ]
@@ -183,11 +187,10 @@ def test_switching_schedules_mid_run(pkg):
     s.close()
 
 
-@pytest.mark.parametrize("W,H,N,T,r", [(40, 40, 256, 1024, 6), (40, 40, 1024, 8, 6),
-                                       (12, 40, 16, 64, 6), (40, 6, 16, 64, 3)])
+@pytest.mark.parametrize("W,H,N,T,r", [(40, 40, 1024, 8, 6), (12, 40, 16, 64, 6),
+                                       (40, 6, 16, 64, 3)])
 def test_tensor_schedule_refused_outside_its_domain(pkg, W, H, N, T, r):
-    """Centred products that could leave the exact range of f32 (T N^2 > 2^25), counts of 1024
-    (N = 1024) and tiles narrower than 2 radius + 1 are refused."""
+    """Counts of 1024 (N = 1024) and tiles narrower than 2 radius + 1 are refused."""
     from paper_2105_12620_gb300 import BnError
     with pytest.raises(BnError):
         pkg.Sampler(W, H, N, T, seed=1, radius=r, schedule=pkg.BN_SCHEDULE_TENSOR)

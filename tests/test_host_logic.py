@@ -103,9 +103,12 @@ def _rank_main(rank: int, world: int, port: int, out):
         # per-rank step times: the job's time is the slowest rank's
         t = bench.all_reduce_list([10.0 + rank, 20.0 - rank], dist, "cpu", "max")
         work = bench.all_reduce_list([100.0 * (rank + 1)], dist, "cpu", "sum")
-        summ = {"p50_latency_s": 1.0 + rank, "p99_latency_s": 3.0 - rank,
-                "p99_queue_s": 0.5 * rank, "makespan_s": 10.0 + 10.0 * rank,
-                "proposals_per_s": 1e6, "completed": 5 + rank}
+        # uneven streams: rank 0 served latencies 0..99 s, rank 1 100..249 s (queue = 1/10)
+        lat = [float(v) for v in (range(100) if rank == 0 else range(100, 250))]
+        summ = {"p50_latency_s": -1.0, "p99_latency_s": -1.0, "p99_queue_s": -1.0,
+                "makespan_s": 10.0 + 10.0 * rank, "proposals_per_s": 1e6,
+                "completed": 5 + rank, "requests": len(lat), "latencies_s": lat,
+                "queue_s": [v / 10 for v in lat]}
         merged = bench.merge_serving(summ, dist, "cpu")
         out.put((rank, t, work, merged))
     finally:
@@ -127,12 +130,33 @@ def test_rank_reductions_world_size_two_gloo():
     for rank, t, work, merged in got:
         assert t == [11.0, 20.0]
         assert work == [300.0]
-        assert merged["p50_latency_s"] == 2.0 and merged["p99_latency_s"] == 3.0
-        assert merged["makespan_s"] == 20.0 and merged["p99_queue_s"] == 0.5
+        # percentiles of the pooled 0..249 (250 samples): order statistic 0.5 * 249 = 124.5
+        # and 0.99 * 249 = 246.51, linearly interpolated; the larger per-rank p50 would be 174.5
+        assert merged["p50_latency_s"] == pytest.approx(124.5)
+        assert merged["p99_latency_s"] == pytest.approx(246.51)
+        assert merged["p99_queue_s"] == pytest.approx(24.651)
+        assert merged["latency_samples"] == 250 and merged["requests"] == 250
+        assert "latencies_s" not in merged and "queue_s" not in merged
+        assert merged["makespan_s"] == 20.0
         # rank 0: 1e6/s over 10 s, rank 1: 1e6/s over 20 s -> 3e7 proposals in 20 s
         assert merged["proposals_per_s"] == pytest.approx(1.5e6)
         assert merged["completed"] == 11
         assert merged["served_req_per_s"] == pytest.approx(11 / 20.0)
+
+
+def test_single_rank_serving_summary_keeps_its_percentiles():
+    from paper_2105_12620_gb300 import serving as srv
+    lat = [0.5, 0.1, 0.3, 0.2, 0.4]
+    pct = srv.latency_percentiles(lat, [0.0] * 5)
+    assert pct["p50_latency_s"] == pytest.approx(0.3)
+    # order statistic 0.99 * 4 = 3.96 of the sorted 0.1 .. 0.5: 0.4 + 0.96 * 0.1
+    assert pct["p99_latency_s"] == pytest.approx(0.496)
+    assert srv.latency_percentiles([], [])["p99_latency_s"] is None
+    summ = {**pct, "latencies_s": lat, "queue_s": [0.0] * 5, "makespan_s": 1.0,
+            "completed": 5, "requests": 5, "proposals_per_s": 1.0}
+    merged = bench.merge_serving(summ, None, "cpu")
+    assert merged["p50_latency_s"] == pct["p50_latency_s"]
+    assert merged["latency_samples"] == 5 and "latencies_s" not in merged
 
 
 def test_workload_definitions():
