@@ -604,7 +604,7 @@ def run_ours(args) -> int:
     extra = {}
     if args.workload == "c2":
         for name in args.extra_workloads.split(","):
-            if name:
+            if name and name != "none":
                 extra[name] = run_extra_workload(pkg, args, name, stream, rank, world, dist)
     serving = serving_light = None
     if args.serving_requests > 0 and args.workload == "c2":
@@ -799,7 +799,7 @@ def main(argv=None) -> int:
     ap.add_argument("--tsplit", type=int, default=1)
     ap.add_argument("--extra-workloads", default="c3,c4",
                     help="workloads timed after the headline and reported beside it (c3, c4; "
-                         "empty skips them)")
+                         "'none' skips them)")
     ap.add_argument("--extra-steps", type=int, default=2,
                     help="timed steps of each extra workload (warm-up: --warmup)")
     ap.add_argument("--serving-requests", type=int, default=500,

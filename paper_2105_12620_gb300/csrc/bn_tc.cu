@@ -1352,9 +1352,9 @@ cudaError_t launch_tc_sweep(const TcLaunch &tl, cudaStream_t st, KernelTimer *tm
     if (all) tm->end(st);
     if (tl.total_units > 0) {
         // each CTA takes a contiguous run of at most kUnitTab patches; a pass with more
-        // patches than the SMs hold that way is split over several launches
-        int per = (tl.total_units + tl.sms - 1) / tl.sms;
-        per = per < kUnitTab ? per : kUnitTab;
+        // patches than the SMs hold that way is split over launches of equal size
+        const int nl = (tl.total_units + kUnitTab * tl.sms - 1) / (kUnitTab * tl.sms);
+        const int per = (tl.total_units + nl * tl.sms - 1) / (nl * tl.sms);
         if (timed) tm->begin(kKTcStencil, st);
         for (int b0 = 0; b0 < tl.total_units; b0 += per * tl.sms) {
             const int cnt = tl.total_units - b0 < per * tl.sms ? tl.total_units - b0 : per * tl.sms;
