@@ -49,6 +49,10 @@ REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 # of k_persistent for 128x128 N=64 T=1024); a launch's traffic scales with its tile-passes
 TRAFFIC_PER_TILE_PASS = (1683.924e6 + 58.356e6) / (16 * 6)
 PASSES_PER_LAUNCH = 500
+# DRAM bytes (read + write) per tile-pass of the tensor-core stencil on the same tiles: one ncu
+# capture of one launch over 16 tiles (the profile summary of k_tc_stencil for 128x128 N=64
+# T=1024); a launch's traffic scales with the tiles it covers
+TC_TRAFFIC_PER_TILE_PASS = (349.900032e6 + 5.298176e6) / 16
 # shared-memory wavefront rate: 128 B per SM clock, measured 120 B/clk/SM by a probe
 SMEM_PEAK_TBS = 152 * 120 * 2.07e9 / 1e12
 
@@ -378,8 +382,12 @@ def kernel_roofline(ktimes: dict, specs, split_steps: int, sweeps: int, args, ch
         tpeak, tsrc = measured_peak("bf16_tflops_sustained")
         tf = 2.0 * total_ops / secs / 1e12
         alu_peak = IMAD_PEAK_TOPS if wide else DP4A_PEAK_TOPS
+        traffic = None
+        if args.workload == "c2" and not wide:
+            # per launch: the tile-passes of the split run over its stencil launches
+            traffic = TC_TRAFFIC_PER_TILE_PASS * len(specs) * split_steps * sweeps / nl
         return {"kernel": name, "bound": "tensor", "achieved": tf, "peak": tpeak,
-                "unit": "TFLOP/s", "frac": tf / tpeak, "traffic": None,
+                "unit": "TFLOP/s", "frac": tf / tpeak, "traffic": traffic,
                 "note": "useful f16 FLOPs of the stencil (2 per kept product); peak = dense "
                         "bf16 sustained " + tsrc,
                 "launches": nl, "avg_launch_ms": tms / nl, "share": tms / max(all_ms, 1e-9),
