@@ -1134,7 +1134,8 @@ __device__ __forceinline__ void axis_patches(int c, int r, int n, int ps, int (&
 // written for every stage of 64 integrands, and each of its two pixels is appended to the lists
 // of the patches within the radius of it (lanes 0-15: pixel a, 16-31: pixel b, one patch per
 // lane).
-__global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
+// eight CTAs of 256 threads per SM (32 registers): occupancy over the few spills it costs
+__global__ void __launch_bounds__(kListThreads, 8) k_tc_lists(const Problem *probs)
 {
     const Problem &pb = probs[blockIdx.y];
     const long long s = pb.ctr[0];
@@ -1150,45 +1151,69 @@ __global__ void __launch_bounds__(kListThreads) k_tc_lists(const Problem *probs)
         reinterpret_cast<int4 *>(pb.side_cls + (size_t)j * 2 * kMaxClasses)[lane] =
             make_int4(0, 0, 0, 0);
     const int kst = tc_stages(pb);
+    // two steps (v, v + 32) per lane and iteration, both steps' loads issued before either
+    // step's stores
     if (pb.count_bytes == 1) {
         // 16 integrands (two f16 pieces of one stage) per lane and step
         const int nv = kst * 4;
-        for (int v = lane; v < nv; v += 32) {
-            const int e0 = v * 16;  // first integrand
-            const size_t cb = ((size_t)(e0 >> 7) * pb.P) << 7;
-            const uint4 ka = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)a << 7) +
-                                                              (e0 & 127));
-            const uint4 kb = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)b << 7) +
-                                                              (e0 & 127));
-            uint4 o0, o1;
-            bytes_sub_h2(kb.x, ka.x, o0.x, o0.y);
-            bytes_sub_h2(kb.y, ka.y, o0.z, o0.w);
-            bytes_sub_h2(kb.z, ka.z, o1.x, o1.y);
-            bytes_sub_h2(kb.w, ka.w, o1.z, o1.w);
-            uint4 *dst = reinterpret_cast<uint4 *>(pb.tc_delta16 +
-                                                   (((size_t)(v >> 2) * pb.M + j) << 6) +
-                                                   (v & 3) * 16);
-            dst[0] = o0;
-            dst[1] = o1;
+        for (int v = lane; v < nv; v += 64) {
+            const bool two = v + 32 < nv;
+            uint4 ka[2], kb[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e0 = (v + 32 * h) * 16;  // first integrand
+                const size_t off = (((size_t)(e0 >> 7) * pb.P) << 7) + (e0 & 127);
+                ka[h] = kb[h] = make_uint4(0u, 0u, 0u, 0u);
+                if (h == 0 || two) {
+                    ka[h] = *reinterpret_cast<const uint4 *>(pb.counts + ((size_t)a << 7) + off);
+                    kb[h] = *reinterpret_cast<const uint4 *>(pb.counts + ((size_t)b << 7) + off);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int vh = v + 32 * h;
+                if (h == 1 && !two) break;
+                uint4 o0, o1;
+                bytes_sub_h2(kb[h].x, ka[h].x, o0.x, o0.y);
+                bytes_sub_h2(kb[h].y, ka[h].y, o0.z, o0.w);
+                bytes_sub_h2(kb[h].z, ka[h].z, o1.x, o1.y);
+                bytes_sub_h2(kb[h].w, ka[h].w, o1.z, o1.w);
+                uint4 *dst = reinterpret_cast<uint4 *>(pb.tc_delta16 +
+                                                       (((size_t)(vh >> 2) * pb.M + j) << 6) +
+                                                       (vh & 3) * 16);
+                dst[0] = o0;
+                dst[1] = o1;
+            }
         }
     } else {
         // 16-bit counts (below 1024): 8 integrands (one f16 piece) per lane and step; a stage
         // of 64 integrands is one 128-byte chunk
         const int nv = kst * 8;
-        for (int v = lane; v < nv; v += 32) {
-            const int e0 = v * 8;
-            const size_t cb = ((size_t)(e0 >> 6) * pb.P) << 7;
-            const uint4 ka = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)a << 7) +
-                                                              (e0 & 63) * 2);
-            const uint4 kb = *reinterpret_cast<const uint4 *>(pb.counts + cb + ((size_t)b << 7) +
-                                                              (e0 & 63) * 2);
-            uint4 o;
-            o.x = h2_sub(kb.x | kH2Magic, ka.x | kH2Magic);
-            o.y = h2_sub(kb.y | kH2Magic, ka.y | kH2Magic);
-            o.z = h2_sub(kb.z | kH2Magic, ka.z | kH2Magic);
-            o.w = h2_sub(kb.w | kH2Magic, ka.w | kH2Magic);
-            *reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(e0 >> 6) * pb.M + j) << 6) +
-                                       (e0 & 63)) = o;
+        for (int v = lane; v < nv; v += 64) {
+            const bool two = v + 32 < nv;
+            uint4 ka[2], kb[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e0 = (v + 32 * h) * 8;
+                const size_t off = (((size_t)(e0 >> 6) * pb.P) << 7) + (e0 & 63) * 2;
+                ka[h] = kb[h] = make_uint4(0u, 0u, 0u, 0u);
+                if (h == 0 || two) {
+                    ka[h] = *reinterpret_cast<const uint4 *>(pb.counts + ((size_t)a << 7) + off);
+                    kb[h] = *reinterpret_cast<const uint4 *>(pb.counts + ((size_t)b << 7) + off);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e0 = (v + 32 * h) * 8;
+                if (h == 1 && !two) break;
+                uint4 o;
+                o.x = h2_sub(kb[h].x | kH2Magic, ka[h].x | kH2Magic);
+                o.y = h2_sub(kb[h].y | kH2Magic, ka[h].y | kH2Magic);
+                o.z = h2_sub(kb[h].z | kH2Magic, ka[h].z | kH2Magic);
+                o.w = h2_sub(kb[h].w | kH2Magic, ka[h].w | kH2Magic);
+                *reinterpret_cast<uint4 *>(pb.tc_delta16 + (((size_t)(e0 >> 6) * pb.M + j) << 6) +
+                                           (e0 & 63)) = o;
+            }
         }
     }
     // lanes 0..15 list pixel a, lanes 16..31 pixel b, one patch each, all atomics in parallel
