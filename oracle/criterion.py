@@ -17,8 +17,15 @@ Readings (the paper leaves these open):
     (not periodic), cx, cy, s drawn from Philox with tag 7: cx = w0 2^-32, cy = w1 2^-32,
     s = 0.05 + 0.45 w2 2^-32; reference integral in closed form with erf.
 
-Plain numpy in float64; np.fft serves as the library primitive of the periodic convolution.
-Only the tests use this module.
+Fig. 1b shows the Fourier spectrum of the tile of estimates: the error of an optimised tile has
+little power at low frequencies.  `error_spectrum` gives its radial average (readings: the power
+of integrand t at frequency (u, v) is |F_t(u, v)|^2 / (W H), F_t the 2-D DFT of the error tile, so
+white error of variance s^2 has power s^2 everywhere; frequencies are grouped into rings by their
+rounded radius in cycles per pixel times min(W, H); the spectrum is the mean over integrands and
+over the frequencies of each ring).
+
+Plain numpy in float64; np.fft serves as the library primitive of the periodic convolution and
+of the spectrum.  Only the tests use this module.
 """
 from __future__ import annotations
 
@@ -149,3 +156,38 @@ def blur(err: np.ndarray, sigma: float) -> np.ndarray:
 def rmse(err: np.ndarray, sigmas) -> np.ndarray:
     """Criterion per sigma: sqrt(mean of the squared filtered error) over integrands and pixels."""
     return np.array([math.sqrt(float(np.mean(blur(err, s) ** 2))) for s in sigmas])
+
+
+# ---------------------------------------------------------------------------------------------
+# the error spectrum (Fig. 1b)
+# ---------------------------------------------------------------------------------------------
+def ring_of(fx: int, fy: int, W: int, H: int) -> int:
+    """Ring of the signed frequency (fx, fy) of a W x H tile: floor(rho L + 1/2) with
+    rho = sqrt((fx / W)^2 + (fy / H)^2) cycles per pixel and L = min(W, H), i.e. the largest b
+    with (2b - 1) W H <= 2 L sqrt((fx H)^2 + (fy W)^2); decided exactly in integers."""
+    S = (fx * H) ** 2 + (fy * W) ** 2
+    m = math.isqrt(4 * min(W, H) ** 2 * S)   # floor(2 L sqrt(S))
+    return (m // (W * H) + 1) // 2
+
+
+def rings(W: int, H: int) -> tuple[np.ndarray, int]:
+    """[H, W] ring of every DFT bin in np.fft.fft2 order (index u is the frequency u, or u - W
+    above W / 2; likewise v), and the number of rings."""
+    ring = np.zeros((H, W), np.int64)
+    for v in range(H):
+        fy = v if 2 * v <= H else v - H
+        for u in range(W):
+            fx = u if 2 * u <= W else u - W
+            ring[v, u] = ring_of(fx, fy, W, H)
+    return ring, int(ring.max()) + 1
+
+
+def error_spectrum(err: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Radially averaged power spectrum of the error tiles err [T, H, W]: (power per ring, number
+    of frequencies per ring); power = mean over t and over the ring of |F_t|^2 / (W H)."""
+    T, H, W = err.shape
+    ring, n = rings(W, H)
+    pw = (np.abs(np.fft.fft2(err, axes=(1, 2))) ** 2).mean(axis=0) / (W * H)
+    counts = np.bincount(ring.ravel(), minlength=n)
+    sums = np.bincount(ring.ravel(), weights=pw.ravel(), minlength=n)
+    return sums / counts, counts

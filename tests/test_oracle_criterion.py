@@ -137,3 +137,75 @@ def test_optimised_tile_lowers_filtered_error_for_both_integrand_kinds():
     assert abs(cr.rmse(cr.heaviside_errors(t.k, t.N, t.a, t.b, t.C, W, H), [0.0])[0]
                - cr.rmse(cr.heaviside_errors(oracle.OracleTile(W, H, 16, 64, seed=3).k, 16,
                                              t.a, t.b, t.C, W, H), [0.0])[0]) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# error spectrum (Fig. 1b)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("fx,fy,W,H,want", [
+    (0, 0, 32, 32, 0), (1, 0, 32, 32, 1), (3, 4, 32, 32, 5), (1, 1, 32, 32, 1),
+    (2, 2, 32, 32, 3), (16, 16, 32, 32, 23), (-7, 2, 32, 32, 7),
+    # 2:1 tile: (1, 0) lies exactly half way, rho L = 1/2, and rounds up
+    (1, 0, 64, 32, 1), (0, 1, 64, 32, 1), (3, 0, 64, 32, 2), (32, 16, 64, 32, 23),
+])
+def test_ring_of_known_values(fx, fy, W, H, want):
+    assert cr.ring_of(fx, fy, W, H) == want
+
+
+def test_ring_of_agrees_with_the_float_radius_off_the_half_way_points():
+    rng = np.random.default_rng(8)
+    for _ in range(2000):
+        W, H = (int(v) for v in rng.integers(2, 300, 2))
+        fx, fy = int(rng.integers(-W // 2, W // 2 + 1)), int(rng.integers(-H // 2, H // 2 + 1))
+        r = math.hypot(fx / W, fy / H) * min(W, H)
+        if abs(r - math.floor(r) - 0.5) > 1e-9:
+            assert cr.ring_of(fx, fy, W, H) == math.floor(r + 0.5)
+
+
+def test_spectrum_against_the_dft_by_definition():
+    """np.fft against the DFT sum written out, on small tiles (even and odd sides)."""
+    rng = np.random.default_rng(3)
+    for W, H in ((6, 4), (5, 3), (7, 7)):
+        err = rng.normal(size=(3, H, W))
+        power, counts = cr.error_spectrum(err)
+        ring, n = cr.rings(W, H)
+        want = np.zeros(n)
+        for t in range(3):
+            for v in range(H):
+                for u in range(W):
+                    F = sum(err[t, y, x] * complex(math.cos(2 * math.pi * (u * x / W + v * y / H)),
+                                                   -math.sin(2 * math.pi * (u * x / W + v * y / H)))
+                            for y in range(H) for x in range(W))
+                    want[ring[v, u]] += abs(F) ** 2 / (W * H)
+        want /= 3 * counts
+        assert np.allclose(power, want, rtol=1e-10, atol=1e-14)
+        assert counts.sum() == W * H
+
+
+def test_spectrum_parseval_and_a_single_cosine():
+    rng = np.random.default_rng(4)
+    err = rng.normal(0, 0.3, size=(5, 24, 40))
+    power, counts = cr.error_spectrum(err)
+    # Parseval: the ring sums add up to the mean squared error per pixel times W H / (W H)
+    assert abs((power * counts).sum() - (err ** 2).sum(axis=(1, 2)).mean()) < 1e-9
+    # cos(2 pi 3 x / W): all power at fx = +-3, fy = 0, each |F|^2 / P = P / 4
+    W = H = 32
+    x = np.arange(W)
+    e = np.tile(np.cos(2 * math.pi * 3 * x / W), (H, 1))[None]
+    power, counts = cr.error_spectrum(e)
+    total = power * counts
+    assert abs(total[3] - W * H / 2) < 1e-9 and abs(total.sum() - W * H / 2) < 1e-9
+
+
+def test_optimised_tile_has_less_low_frequency_error_power():
+    """Fig. 1b: after the optimisation the error's power at low frequencies drops, while the
+    total (the per-pixel error multiset is only permuted) stays the same."""
+    W = H = 32
+    t = oracle.OracleTile(W, H, 16, 64, seed=5)
+    p0, c = cr.error_spectrum(cr.heaviside_errors(t.k, t.N, t.a, t.b, t.C, W, H))
+    for _ in range(120):
+        t.sweep()
+    p1, _ = cr.error_spectrum(cr.heaviside_errors(t.k, t.N, t.a, t.b, t.C, W, H))
+    low = slice(1, W // 8 + 1)
+    assert (p1[low] * c[low]).sum() < 0.5 * (p0[low] * c[low]).sum(), (p0[low], p1[low])
+    assert abs((p1 * c).sum() - (p0 * c).sum()) < 1e-12 * (p0 * c).sum()
