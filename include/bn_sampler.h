@@ -253,6 +253,25 @@ int bn_sampler_autotune(bn_sampler *s, int32_t trial_sweeps, bn_schedule *chosen
 int bn_evaluate_criterion(bn_sampler *s, int32_t pair, int32_t integrands, int32_t n_integrands,
                           const float *sigmas, int32_t n_sigma, double *rmse_out);
 
+/* ---- error spectrum (Fig. 1b) -----------------------------------------------------------------
+ * Radially averaged power spectrum of the pair's error tiles e_t(p) = I_p - I_ref, for the same
+ * integrands as bn_evaluate_criterion.  F_t is the 2-D DFT of e_t over the W x H tile; the power
+ * of frequency (u, v) is |F_t(u, v)|^2 / (W H), so white error of variance s^2 has power s^2 at
+ * every frequency and the rings' power x count sums to the mean squared error per pixel (times
+ * W H / W H: Parseval).  Ring of (u, v): f_x = u, or u - W when 2u > W (likewise f_y with H),
+ * rho = sqrt((f_x / W)^2 + (f_y / H)^2) cycles per pixel, ring = floor(rho min(W, H) + 1/2),
+ * decided in exact integer arithmetic; ring 0 holds the mean error (0, 0).
+ *   power_out    host, n_rings doubles: mean over the integrands and over the ring's
+ *                frequencies; null = only report the ring count in *n_rings_out.
+ *   counts_out   host, n_rings int64 (nullable): frequencies per ring.
+ *   n_rings_out  (nullable) receives the ring count, floor(sqrt(1/2) min(W, H) + 1/2) + 1 for a
+ *                square tile; n_rings below it is BN_ERR_INVALID_ARG.
+ * Tile sides at most 1024.  FP64 throughout (direct DFT sums, twiddles computed on the host).
+ * Uses temporary device memory (stream-ordered); synchronises. */
+int bn_error_spectrum(bn_sampler *s, int32_t pair, int32_t integrands, int32_t n_integrands,
+                      double *power_out, int64_t *counts_out, int32_t n_rings,
+                      int32_t *n_rings_out);
+
 /* ---- renderer lookup (Sec. 3.1, Sec. 3.2) ---------------------------------------------------
  * bn_export_shift_table writes the pair's current per-pixel shifts (uint32 [height][width][2],
  * 0.32 fixed point) to device memory (enqueued only), for the device function bn_sample() of

@@ -134,6 +134,8 @@ _SIGS = {
                                                   ctypes.c_float, ctypes.c_int32, _P, _P]),
     "bn_evaluate_criterion": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              _P, ctypes.c_int32, _P]),
+    "bn_error_spectrum": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         _P, _P, ctypes.c_int32, _P]),
     "bn_export_shift_table": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
     "bn_generate_samples": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,

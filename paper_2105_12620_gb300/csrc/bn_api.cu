@@ -900,6 +900,39 @@ int bn_evaluate_criterion(bn_sampler *s, int32_t pair, int32_t integrands, int32
     return BN_OK;
 }
 
+int bn_error_spectrum(bn_sampler *s, int32_t pair, int32_t integrands, int32_t n_integrands,
+                      double *power_out, int64_t *counts_out, int32_t n_rings, int32_t *n_rings_out)
+{
+    bn::TraceRange trace_("bn.error_spectrum");
+    if (int rc = check_pair(s, pair)) return rc;
+    const bn::Problem &h = s->hprob[pair];
+    if (h.W > 1024 || h.H > 1024)
+        return fail(BN_ERR_INVALID_ARG, "the spectrum needs tile sides of at most 1024");
+    const int need = bn::spectrum_rings(h.W, h.H, nullptr);
+    if (n_rings_out) *n_rings_out = need;
+    if (!power_out) return BN_OK;  // a query of the ring count
+    if (n_rings < need) return fail(BN_ERR_INVALID_ARG, "the tile has %d rings", need);
+    if (integrands != BN_INTEGRANDS_HEAVISIDE && integrands != BN_INTEGRANDS_GAUSSIAN)
+        return fail(BN_ERR_INVALID_ARG, "integrands must be BN_INTEGRANDS_HEAVISIDE or _GAUSSIAN");
+    const int most = integrands == BN_INTEGRANDS_HEAVISIDE ? h.T : 4096;
+    if (n_integrands < 1 || n_integrands > most)
+        return fail(BN_ERR_INVALID_ARG, "n_integrands must be in [1, %d]", most);
+    if (int rc = set_device(s)) return rc;
+    std::vector<double> sums(need, 0.0);
+    BN_CUDA(bn::spectrum_sums(s->dprob + pair, h, integrands, n_integrands, sums.data(),
+                              s->stream));
+    if (int rc = check_device_error(s)) return rc;
+    std::vector<int> ring;
+    bn::spectrum_rings(h.W, h.H, &ring);
+    std::vector<int64_t> cnt(need, 0);
+    for (int r : ring) ++cnt[r];
+    for (int b = 0; b < need; ++b) {
+        power_out[b] = sums[b] / ((double)cnt[b] * (double)n_integrands);
+        if (counts_out) counts_out[b] = cnt[b];
+    }
+    return BN_OK;
+}
+
 int bn_export_shift_table(bn_sampler *s, int32_t pair, uint32_t *out_device, size_t n_words)
 {
     if (int rc = check_pair(s, pair)) return rc;

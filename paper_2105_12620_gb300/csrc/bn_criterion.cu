@@ -10,8 +10,15 @@
 // erf differences).  Everything is FP64: the filtered errors at wide sigma are small differences
 // of much larger terms.
 //
+// Spectrum (Fig. 1b): for the same error tiles, F_t = the 2-D DFT of e_t (rows, then columns,
+// as direct sums with twiddle tables computed on the host in FP64), and the power |F_t|^2 / (W H)
+// summed per ring of frequencies: ring = floor(rho min(W, H) + 1/2), rho the radius in cycles per
+// pixel, decided in exact integer arithmetic; the mean over integrands and ring members is
+// formed on the host.
+//
 // Layout of the scratch (per batch of B integrands): err and tmp double [P][B], integrand index
-// fastest, so a warp reads B consecutive doubles of one pixel.
+// fastest, so a warp reads B consecutive doubles of one pixel; the row transforms double2
+// [H][W][B] (row y, frequency u).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -168,6 +175,60 @@ __global__ void __launch_bounds__(kCritThreads)
     }
 }
 
+// R[y][u][i] = sum_x e[y][x][i] tw[u x mod W], tw[k] = exp(-2 pi i k / W)
+__global__ void __launch_bounds__(kCritThreads)
+    k_dft_rows(int W, int H, int B, const double *err, const double2 *tw, double2 *R)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)W * H * B) return;
+    const int i = (int)(idx % B);
+    const int c = (int)(idx / B);  // y W + u
+    const int u = c % W, y = c / W;
+    const double *row = err + (size_t)y * W * B + i;
+    double re = 0.0, im = 0.0;
+    int k = 0;  // u x mod W
+    for (int x = 0; x < W; ++x) {
+        const double e = row[(size_t)x * B];
+        const double2 w = tw[k];
+        re = fma(e, w.x, re);
+        im = fma(e, w.y, im);
+        k += u;
+        k -= k >= W ? W : 0;
+    }
+    R[idx] = make_double2(re, im);
+}
+
+// F[v][u][i] = sum_y R[y][u][i] tw[v y mod H]; |F|^2 / (W H) added to the ring of (u, v) in
+// sums (per-block partial sums in shared memory first)
+__global__ void __launch_bounds__(kCritThreads)
+    k_dft_cols_power(int W, int H, int B, const double2 *R, const double2 *tw, const int *ring,
+                     int n_rings, double *sums)
+{
+    extern __shared__ double sring[];  // [n_rings]
+    for (int r = threadIdx.x; r < n_rings; r += blockDim.x) sring[r] = 0.0;
+    __syncthreads();
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < (long long)W * H * B) {
+        const int i = (int)(idx % B);
+        const int c = (int)(idx / B);  // v W + u
+        const int u = c % W, v = c / W;
+        double re = 0.0, im = 0.0;
+        int k = 0;  // v y mod H
+        for (int y = 0; y < H; ++y) {
+            const double2 r = R[((size_t)y * W + u) * B + i];
+            const double2 w = tw[k];
+            re = fma(r.x, w.x, fma(-r.y, w.y, re));
+            im = fma(r.x, w.y, fma(r.y, w.x, im));
+            k += v;
+            k -= k >= H ? H : 0;
+        }
+        atomicAdd(&sring[ring[c]], (re * re + im * im) / ((double)W * (double)H));
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n_rings; r += blockDim.x)
+        if (sring[r] != 0.0) atomicAdd(&sums[r], sring[r]);
+}
+
 // renderer lookup into out[r][i][j][d] for screen pixels (x0 + i, y0 + r), samples first + j
 __global__ void k_samples(bn_sample_table tb, int x0, int y0, int width, int height, int first,
                           int count, int n_dims, float *out)
@@ -221,7 +282,108 @@ void gaussian_taps(int n, double sigma, std::vector<int> &off, std::vector<doubl
         }
 }
 
+// floor(sqrt(x)) for x < 2^62
+unsigned long long isqrt_u64(unsigned long long x)
+{
+    unsigned long long m = (unsigned long long)std::sqrt((double)x);
+    while (m > 0 && m * m > x) --m;
+    while ((m + 1) * (m + 1) <= x) ++m;
+    return m;
+}
+
 }  // namespace
+
+int spectrum_ring(int fx, int fy, int W, int H)
+{
+    // the largest b with (2b - 1) W H <= 2 L sqrt(S), S = (fx H)^2 + (fy W)^2, L = min(W, H):
+    // with m = floor(2 L sqrt(S)), b = (floor(m / (W H)) + 1) / 2
+    const unsigned long long L = (unsigned long long)(W < H ? W : H);
+    const unsigned long long S = (unsigned long long)((long long)fx * H * fx * H) +
+                                 (unsigned long long)((long long)fy * W * fy * W);
+    const unsigned long long m = isqrt_u64(4ull * L * L * S);
+    return (int)((m / ((unsigned long long)W * (unsigned long long)H) + 1ull) / 2ull);
+}
+
+int spectrum_rings(int W, int H, std::vector<int> *ring)
+{
+    int n = 0;
+    if (ring) ring->assign((size_t)W * H, 0);
+    for (int v = 0; v < H; ++v) {
+        const int fy = 2 * v <= H ? v : v - H;
+        for (int u = 0; u < W; ++u) {
+            const int fx = 2 * u <= W ? u : u - W;
+            const int r = spectrum_ring(fx, fy, W, H);
+            if (ring) (*ring)[(size_t)v * W + u] = r;
+            n = r + 1 > n ? r + 1 : n;
+        }
+    }
+    return n;
+}
+
+cudaError_t spectrum_sums(const Problem *dprob, const Problem &h, int kind, int n_int,
+                          double *sums, cudaStream_t st)
+{
+    const int P = h.P, W = h.W, H = h.H;
+    std::vector<int> hring;
+    const int n_rings = spectrum_rings(W, H, &hring);
+    int B = (int)std::min<long long>(128, std::max<long long>(1, (1ll << 26) / P));
+    B = std::min(B, n_int);
+    std::vector<double2> hw((size_t)W + H);
+    for (int k = 0; k < W; ++k)
+        hw[k] = make_double2(std::cos(2.0 * M_PI * k / W), -std::sin(2.0 * M_PI * k / W));
+    for (int k = 0; k < H; ++k)
+        hw[(size_t)W + k] = make_double2(std::cos(2.0 * M_PI * k / H), -std::sin(2.0 * M_PI * k / H));
+    double *err = nullptr, *ref = nullptr, *dsum = nullptr;
+    double2 *R = nullptr, *dtw = nullptr;
+    int *dring = nullptr;
+    Bump *bank = nullptr;
+    cudaError_t e = cudaMallocAsync(&err, sizeof(double) * (size_t)P * B, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&R, sizeof(double2) * (size_t)P * B, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&ref, sizeof(double) * B, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&bank, sizeof(Bump) * B, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dsum, sizeof(double) * n_rings, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dtw, sizeof(double2) * hw.size(), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dring, sizeof(int) * hring.size(), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtw, hw.data(), sizeof(double2) * hw.size(), cudaMemcpyHostToDevice,
+                            st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dring, hring.data(), sizeof(int) * hring.size(),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, sizeof(double) * n_rings, st);
+    int launches = 0;
+    for (int first = 0; e == cudaSuccess && first < n_int; first += B) {
+        const int nb = std::min(B, n_int - first);
+        const long long cells = (long long)P * nb;
+        const int grid = (int)((cells + kCritThreads - 1) / kCritThreads);
+        if (kind == BN_INTEGRANDS_HEAVISIDE) {
+            k_heaviside_refs<<<(nb + 127) / 128, 128, 0, st>>>(dprob, first, nb, ref);
+            if (h.count_bytes == 1)
+                k_err_heaviside<uint8_t><<<grid, kCritThreads, 0, st>>>(dprob, first, nb, ref, err);
+            else
+                k_err_heaviside<uint16_t><<<grid, kCritThreads, 0, st>>>(dprob, first, nb, ref,
+                                                                         err);
+        } else {
+            k_bump_bank<<<(nb + 127) / 128, 128, 0, st>>>(dprob, first, nb, bank);
+            k_err_bumps<<<(P * 32 + kCritThreads - 1) / kCritThreads, kCritThreads, 0, st>>>(
+                dprob, nb, bank, err);
+        }
+        k_dft_rows<<<grid, kCritThreads, 0, st>>>(W, H, nb, err, dtw, R);
+        k_dft_cols_power<<<grid, kCritThreads, sizeof(double) * n_rings, st>>>(
+            W, H, nb, R, dtw + W, dring, n_rings, dsum);
+        launches += 4;
+        e = cudaGetLastError();
+    }
+    note_launches(launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sums, dsum, sizeof(double) * n_rings, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (void *ptr : {(void *)err, (void *)R, (void *)ref, (void *)bank, (void *)dsum,
+                      (void *)dtw, (void *)dring})
+        if (ptr) cudaFreeAsync(ptr, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    return e != cudaSuccess ? e : e2;
+}
 
 cudaError_t criterion_sums(const Problem *dprob, const Problem &h, int kind, int n_int,
                            const float *sigmas, int n_sigma, double *sums, cudaStream_t st)

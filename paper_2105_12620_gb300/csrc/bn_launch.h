@@ -48,6 +48,13 @@ cudaError_t criterion_sums(const Problem *dprob, const Problem &h, int kind, int
                            const float *sigmas, int n_sigma, double *sums, cudaStream_t st);
 cudaError_t launch_shift_table(const Problem *dprob, const Problem &h, uint32_t *out,
                                cudaStream_t st);
+// error spectrum: ring of a signed frequency, the rings of a W x H tile (ring table [H][W] in DFT
+// order when ring is not null; returns the ring count), and the per-ring sums of |F_t|^2 / (W H)
+// over the first n_int integrands (host sums[ring count]; synchronises)
+int spectrum_ring(int fx, int fy, int W, int H);
+int spectrum_rings(int W, int H, std::vector<int> *ring);
+cudaError_t spectrum_sums(const Problem *dprob, const Problem &h, int kind, int n_int,
+                          double *sums, cudaStream_t st);
 cudaError_t launch_samples(const bn_sample_table &tb, int x0, int y0, int width, int height,
                            int first, int count, int n_dims, float *out, cudaStream_t st);
 

@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(kPlainThreads) k_eval_plain(const Problem *pro
         atomicAdd(&pb.stats[threadIdx.x], (unsigned long long)bstat[threadIdx.x]);
 }
 
-__global__ void __launch_bounds__(kPlainThreads) k_resolve_plain(const Problem *probs)
+// eight CTAs of 256 threads per SM (32 registers): more owner loads in flight, a few spills
+__global__ void __launch_bounds__(kPlainThreads, 8) k_resolve_plain(const Problem *probs)
 {
     const Problem &pb = probs[blockIdx.y];
     const long long s = pb.ctr[0];

@@ -151,6 +151,22 @@ class Sampler:
                                                out.ctypes.data))
         return out
 
+    def spectrum(self, integrands: str = "heaviside", n_integrands: int | None = None,
+                 pair: int = 0) -> tuple[np.ndarray, np.ndarray]:
+        """Radially averaged power spectrum of the error tiles (Fig. 1b): (power per ring,
+        frequencies per ring)."""
+        kind = {"heaviside": L.BN_INTEGRANDS_HEAVISIDE, "gaussian": L.BN_INTEGRANDS_GAUSSIAN}[
+            integrands]
+        n = n_integrands if n_integrands else (self.n_integrands if kind == 0 else 256)
+        nr = ctypes.c_int32()
+        L.check(L.load().bn_error_spectrum(self._h, pair, kind, n, None, None, 0,
+                                           ctypes.byref(nr)))
+        power = np.zeros(nr.value, np.float64)
+        counts = np.zeros(nr.value, np.int64)
+        L.check(L.load().bn_error_spectrum(self._h, pair, kind, n, power.ctypes.data,
+                                           counts.ctypes.data, nr.value, ctypes.byref(nr)))
+        return power, counts
+
     def shift_table_into(self, pair: int, device_ptr: int, n_words: int) -> None:
         """Current per-pixel shifts (uint32 [H][W][2]) into device memory, for bn_sample()."""
         L.check(L.load().bn_export_shift_table(self._h, pair, device_ptr, n_words))

@@ -112,6 +112,79 @@ def test_optimisation_lowers_the_filtered_error_on_gpu(pkg):
     s.close()
 
 
+def _oracle_spectrum(ref, kind, n):
+    if kind == "heaviside":
+        err = cr.heaviside_errors(ref.k[:, :n], ref.N, ref.a[:n], ref.b[:n], ref.C[:n], ref.W,
+                                  ref.H)
+    else:
+        err = cr.bump_errors(ref.N, ref.g, ref.U[ref.sidx], cr.bump_bank(ref.seed, ref.pair, n),
+                             ref.W, ref.H)
+    return cr.error_spectrum(err)
+
+
+def _spectra_close(got, want, rtol):
+    # the direct DFT and numpy's FFT round differently: relative to each ring, with a floor of
+    # 1e-12 of the largest ring for rings that hold almost no power
+    (pg, cg), (pw, cw) = got, want
+    assert np.array_equal(cg, cw)
+    np.testing.assert_allclose(pg, pw, rtol=rtol, atol=1e-12 * pw.max())
+
+
+@pytest.mark.parametrize("cfg", [
+    # (W, H, N, T, pairs, seed, n_bumps)
+    (24, 20, 16, 64, 1, 3, 12),
+    (13, 17, 128, 40, 1, 4, 9),       # 16-bit counts, odd sides
+    (40, 20, 64, 100, 2, 5, 10),      # 2:1 tile (rings of half-way frequencies), two pairs
+    (5, 3, 4, 9, 1, 6, 5),            # tiny torus
+])
+def test_spectrum_matches_oracle(pkg, cfg):
+    W, H, N, T, pairs, seed, nb = cfg
+    s = pkg.Sampler(W, H, N, T, seed=seed, n_pairs=pairs)
+    for pair in range(pairs):
+        ref = oracle.OracleTile(W, H, N, T, seed=seed, pair=pair)
+        for kind, n, rtol in (("heaviside", T, RTOL_H), ("heaviside", max(1, T // 3), RTOL_H),
+                              ("gaussian", nb, RTOL_B)):
+            _spectra_close(s.spectrum(kind, n, pair), _oracle_spectrum(ref, kind, n), rtol)
+    s.close()
+
+
+def test_spectrum_full_size_and_low_frequencies_after_optimisation(pkg):
+    """128 x 128, N = 64, T = 1024 against the oracle; then Fig. 1b's claim in lockstep: after the
+    optimisation the error power in the lowest rings drops, the total stays (a swap permutes the
+    per-pixel errors)."""
+    W = H = 128
+    s = pkg.Sampler(W, H, 64, 1024, seed=0)
+    ref = oracle.OracleTile(W, H, 64, 1024, seed=0)
+    p0 = s.spectrum("heaviside")
+    _spectra_close(p0, _oracle_spectrum(ref, "heaviside", 1024), RTOL_H)
+    small = pkg.Sampler(32, 32, 16, 64, seed=9)
+    sref = oracle.OracleTile(32, 32, 16, 64, seed=9)
+    q0, c = small.spectrum("heaviside")
+    _lockstep(small, [sref], 120)
+    q1, _ = small.spectrum("heaviside")
+    _spectra_close((q1, c), _oracle_spectrum(sref, "heaviside", 64), RTOL_H)
+    low = slice(1, 32 // 8 + 1)
+    # 0.57 after 80 passes of this tile
+    assert (q1[low] * c[low]).sum() < 0.7 * (q0[low] * c[low]).sum(), (q0[low], q1[low])
+    assert abs((q1 * c).sum() - (q0 * c).sum()) < 1e-9 * (q0 * c).sum()
+    small.close()
+    s.close()
+
+
+def test_spectrum_rejects_bad_arguments(pkg):
+    from paper_2105_12620_gb300 import BnError
+    s = pkg.Sampler(16, 16, 16, 32, seed=1)
+    with pytest.raises(BnError):
+        s.spectrum("heaviside", 33)
+    with pytest.raises(BnError):
+        s.spectrum("gaussian", 5000)
+    s.close()
+    big = pkg.Sampler(1100, 8, 4, 8, seed=1)
+    with pytest.raises(BnError):
+        big.spectrum("heaviside")
+    big.close()
+
+
 def test_criterion_rejects_bad_arguments(pkg):
     from paper_2105_12620_gb300 import BnError
     s = pkg.Sampler(16, 16, 16, 32, seed=1)
