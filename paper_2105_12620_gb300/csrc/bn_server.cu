@@ -65,7 +65,7 @@ int ceil_pow2(int v)
 
 std::string signature(const bn_config &c)
 {
-    return std::to_string(c.n_points > 256 ? 2 : 1) + "/" + std::to_string(c.n_points) + "/" +
+    return std::to_string(c.n_points <= 64 ? 1 : 2) + "/" + std::to_string(c.n_points) + "/" +
            std::to_string(c.n_integrands) + "/" + std::to_string(c.radius) + "/" +
            std::to_string(c.n_pairs) + "/" + std::to_string(ceil_pow2(c.width)) + "x" +
            std::to_string(ceil_pow2(c.height));
