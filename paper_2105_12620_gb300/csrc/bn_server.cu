@@ -206,19 +206,27 @@ void loop(bn_server *sv)
                 if (!ok) break;
                 const std::string key = signature(r.req.cfg);
                 auto it = sv->tuned.find(key);
-                if (it == sv->tuned.end()) {
-                    bool tc = sv->cfg.tensor_policy == BN_SERVE_TENSOR_ALWAYS;
+                bool tc = false;
+                if (it != sv->tuned.end()) {
+                    tc = it->second;
+                } else {
+                    tc = sv->cfg.tensor_policy == BN_SERVE_TENSOR_ALWAYS;
+                    bool keep = true;
                     if (sv->cfg.tensor_policy == BN_SERVE_TENSOR_TUNED && bn::tensor_capable(r.s)) {
                         bn::TraceRange trace_("bn.server.tune");
                         bn_schedule best{};
-                        ok = bn::tune_schedule(r.s, kTuneSweeps, &best) == BN_OK;
-                        tc = ok && best.kind == BN_SCHEDULE_TENSOR;
+                        // a trial that fails (no memory for its scratch copy, say) sends the
+                        // request to the other batch and is not cached: a later request of the
+                        // signature tries again
+                        keep = bn::tune_schedule(r.s, kTuneSweeps, &best) == BN_OK;
+                        if (!keep) cudaGetLastError();
+                        tc = keep && best.kind == BN_SCHEDULE_TENSOR;
                         std::lock_guard<std::mutex> lk(sv->mu);
                         ++sv->st.tunes;
                     }
-                    it = sv->tuned.emplace(key, tc).first;
+                    if (keep) sv->tuned.emplace(key, tc);
                 }
-                r.tensor = it->second && bn::tensor_capable(r.s);
+                r.tensor = tc && bn::tensor_capable(r.s);
             }
             for (int g = 0; g < 2 && ok; ++g) {
                 if (sv->batch[g]) bn_batch_destroy(sv->batch[g]);
