@@ -200,3 +200,33 @@ def test_schedule_description_of_the_json_line():
     assert p == {"kind": "persistent", "block": [8, 8], "threads": 256, "tsplit": 1,
                  "chosen_by": "command line"}
     assert bench.schedule_desc({"kind": 1, "shape": (0, 0, 0, 0), "tsplit": 0})["kind"] == "plain"
+
+
+def test_kernel_roofline_of_the_tensor_stencil():
+    """The roofline object of the bench line: kept f16 FLOPs over the stencil's event time, the
+    algorithmic count bytes, and the DRAM traffic of one launch scaled from the capture."""
+    import argparse
+    from paper_2105_12620_gb300 import workloads as wl
+    specs = wl.c2(64)
+    sweeps, split = specs[0].sweeps, 2
+    launches, total_ms = split * sweeps, split * sweeps * 0.432
+    ktimes = {"stencil_tensor": (launches, total_ms), "lists_tensor": (launches, 0.138 * launches)}
+    args = argparse.Namespace(workload="c2")
+    pkg = argparse.Namespace(BN_SCHEDULE_PERSISTENT=2)
+    r = bench.kernel_roofline(ktimes, specs, split, sweeps, args, {"kind": 3}, pkg)
+    P, T = 128 * 128, 1024
+    kept_macs = 64 * (sweeps * P // 8) * 2 * 112 * T * split      # proposals x 2 sides x 112 x T
+    secs = total_ms / 1000
+    assert r["kernel"] == "stencil_tensor" and r["bound"] == "tensor"
+    assert r["achieved"] == pytest.approx(2 * kept_macs / secs / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["avg_launch_ms"] == pytest.approx(0.432)
+    assert r["share"] == pytest.approx(0.432 / (0.432 + 0.138))
+    # one launch per pass at 64 tiles: the per-tile-pass bytes of the capture times 64
+    assert r["traffic"] == pytest.approx(bench.TC_TRAFFIC_PER_TILE_PASS * 64)
+    count_bytes = 64 * P * T * sweeps * split
+    assert r["hbm"]["achieved"] == pytest.approx(count_bytes / secs / 1e9)
+    # another workload: no capture to scale from
+    r3 = bench.kernel_roofline(ktimes, specs, split, sweeps, argparse.Namespace(workload="c4"),
+                               {"kind": 3}, pkg)
+    assert r3["traffic"] is None
