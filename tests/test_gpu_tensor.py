@@ -65,6 +65,12 @@ LOCKSTEP = [
     (31, 33, 512, 300, 2, 3, 11, 4),    # ragged T over rounds of 2 stages, two pairs, radius 3
     (33, 29, 512, 100, 1, 3, 2, 6),     # N = 512 (counts up to 512), radius 3
     (29, 31, 128, 70, 1, 8, 6, 6),      # radius 8 with 16-bit counts
+    # the other radii (class tables of the generic epilogue paths)
+    (27, 25, 16, 96, 1, 2, 14, 8),      # radius 2
+    (30, 22, 64, 160, 1, 4, 15, 6),     # radius 4, ragged patches
+    (36, 28, 256, 300, 1, 5, 16, 4),    # radius 5, 16-bit counts
+    (40, 34, 32, 128, 2, 7, 17, 4),     # radius 7, two pairs
+    (33, 35, 256, 1100, 1, 8, 18, 3),   # radius 8 with two accumulator rounds
 ]
 
 
@@ -150,6 +156,33 @@ def test_tensor_batch_equals_each_alone(pkg):
     for m, (sh, e) in zip(mixed, alone):
         assert np.array_equal(m.shifts(), sh)
         assert np.array_equal(m.energy(), e)
+    b.close()
+    for m in mixed:
+        m.close()
+
+
+def test_tensor_batch_of_mixed_widths_radii_and_rounds(pkg):
+    """One tensor-core batch holding 8-bit and 16-bit problems (separately ordered patches),
+    radii 3, 6 and 8, a problem in two accumulator rounds and a two-pair member, with per-member
+    budgets: every member equals the plain schedule alone."""
+    cfgs = [  # (W, H, N, T, pairs, radius, seed, passes)
+        (48, 40, 16, 256, 1, 6, 1, 12), (40, 36, 256, 1024, 1, 6, 2, 9),
+        (37, 29, 128, 200, 2, 3, 3, 14), (44, 30, 64, 512, 1, 8, 4, 7),
+        (32, 32, 512, 300, 1, 6, 5, 10),
+    ]
+    mixed = [pkg.Sampler(W, H, N, T, seed=seed, n_pairs=p, radius=r,
+                         schedule=pkg.BN_SCHEDULE_TENSOR)
+             for W, H, N, T, p, r, seed, _ in cfgs]
+    b = pkg.Batch(mixed)
+    assert b.get_schedule()["kind"] == pkg.BN_SCHEDULE_TENSOR
+    b.optimize_each([c[-1] for c in cfgs], stats=False)
+    for m, (W, H, N, T, p, r, seed, n) in zip(mixed, cfgs):
+        with pkg.Sampler(W, H, N, T, seed=seed, n_pairs=p, radius=r,
+                         schedule=pkg.BN_SCHEDULE_PLAIN) as a:
+            a.optimize(n, stats=False)
+            assert np.array_equal(m.shifts(), a.shifts())
+            assert np.array_equal(m.energy(), a.energy())
+            assert m.get_state()[0] == a.get_state()[0]
     b.close()
     for m in mixed:
         m.close()
